@@ -1,0 +1,362 @@
+"""Benchmark of the MuCITE ion-pack step on B300.
+
+Workload (one GPU): the S-lens-like ring stack -- 512 x 2048 (r, z) grid,
+20 rings with RF 1 MHz / 100 V peak and DC -2 V per ring, free-jet N2
+1000 -> 100 Pa, 100,000 packs of 15 kDa / +8 / 1500 A^2 / 2000 atoms,
+dt = 0.5 ns. One benchmark step = `--micro` micro steps of every pack
+(gather, collisions, kick, drift, classification) followed by the tally of
+the observables. Metric: ion-pack steps per second (active packs advanced
+one dt), FP32 fused path, with the plain FP64 GPU step timed on the same
+workload beside it.
+
+Timing: CUDA events on the library's stream around each benchmark step,
+L2 flushed (256 MiB write) before every timed step, W warm-up steps first,
+max over ranks. With torchrun (N > 1) every rank advances its own
+independent replica (seed + rank): weak scaling, no data-path collective.
+
+--impl reference runs the FP64 CPU oracle (the reference implementation of
+the method here) on the same workload and metric, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ion-pack steps/s (FP32 batched vs plain FP64, same GPU); p50/p99 request latency"
+UNIT = "pack-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(micro=200, n_packs=10_000, seconds_cap=25.0):
+    """The oracle as it stands, on a same-shape sample of the workload."""
+    import numpy as np
+    import oracle
+    from paper_2609_31258_b300 import workloads as W
+    w = W.ring_stack(n_packs=n_packs, n_steps=0, precision=1)
+    s = oracle.Sim(w)
+    s.inject()
+    s.steps(5)
+    n0 = int(s.nsteps.sum())
+    t0 = time.perf_counter()
+    done = 0
+    while done < micro:
+        s.steps(50)
+        done += 50
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    dt = time.perf_counter() - t0
+    ps = int(s.nsteps.sum()) - n0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_packs} packs x {done} micro steps of the same 512x2048 ring-stack workload "
+                      f"({ps} pack-steps in {dt:.1f} s, FP64 C oracle, OpenMP over packs)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    steps = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline_run(micro=50, n_packs=4000, seconds_cap=20.0)
+        if k >= args.warmup:
+            steps.append(r["value"])
+            cb = r
+    val = sum(steps) / len(steps)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "ring-stack 512x2048, 15 kDa/+8 ions, dt 0.5 ns (oracle sample)",
+                      "packs": 4000, "micro_steps_per_step": 50},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mucite", choices=["mucite", "reference"])
+    ap.add_argument("--micro", type=int, default=2000, help="micro steps per benchmark step")
+    ap.add_argument("--packs", type=int, default=100_000)
+    ap.add_argument("--spl", type=int, default=0, help="micro steps fused per launch (0 = tuned default)")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2609_31258_b300 import build, mucite, workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    dev = torch.device("cuda", local)
+    peaks, peak_src = _peaks()
+
+    w = W.ring_stack(n_packs=args.packs, n_steps=0, seed=1 + rank, precision=0)
+    stream = torch.cuda.Stream(dev)
+    ctx = mucite.Context(local, stream)
+    ctx.set_tuning(args.spl or 2000, args.threads or 128)
+    mucite.load_workload(ctx, w, 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def bench_step():
+        ctx.step(0, args.micro)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        bench_step()
+        ctx.tally(0)
+    barrier()
+    T0 = ctx.tally(0)
+    l0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            bench_step()
+            ev[k][1].record(stream)
+        barrier()
+    launches_step = ctx.launch_count() - l0
+    T1 = ctx.tally(0)
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    pack_steps = T1["pack_steps"] - T0["pack_steps"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([pack_steps], device=dev, dtype=torch.float64)
+        dist.all_reduce(p)
+        t_ms, total_ps = float(t.item()), float(p.item())
+    else:
+        total_ps = float(pack_steps)
+    value = total_ps / (t_ms * 1e-3)
+
+    # kernel-level roofline of the fused step kernel: launches of one step
+    launches_per_step = launches_step / args.steps
+    kern_ms = t_ms / args.steps / max(launches_per_step, 1)
+    insts = _inst_per_pack_step()
+    sm_mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    peak_ginst = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9  # lane-instructions/s, in G
+    ach = (value / ws) * insts / 1e9 if insts else None
+    roofline = {"bound": "alu", "achieved": ach, "peak": peak_ginst, "unit": "Ginst/s (thread instructions)",
+                "frac": (ach / peak_ginst) if ach else None, "traffic": _traffic_per_launch(),
+                "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
+                "inst_per_pack_step": insts,
+                "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
+                "hbm_bytes_per_pack_step_at_launch": 57.0 / (args.spl or 2000)}
+
+    # end to end through the C ABI with host buffers: H2D of the pack state
+    # from pinned memory, the steps, D2H of the tally
+    e2e = _e2e(ctx, args, stream, dev)
+
+    # plain FP64 GPU step on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = _fp64(args, w, local, stream, dev)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_run()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": w.name, "grid": "512x2048", "packs_per_gpu": args.packs,
+                          "micro_steps_per_step": args.micro, "steps_per_launch": args.spl or 2000,
+                          "threads_per_block": args.threads or 128,
+                          "l2": "flushed before every timed step (256 MiB write)",
+                          "parallelism": f"replicas x{ws}"},
+               "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+               "gpu_launches": int(launches_step), "fp64_plain": fp64,
+               "speedup_fp32_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
+               "peaks_source": peak_src}
+        print(json.dumps(out))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _inst_per_pack_step():
+    """Thread instructions per active pack-step of the fused kernel, from the
+    committed ncu summary (profiles/step_f32_ring_stack.txt)."""
+    p = os.path.join(ROOT, "profiles", "step_f32_ring_stack.txt")
+    try:
+        for ln in open(p):
+            if ln.startswith("inst_per_pack_step:"):
+                return float(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def _traffic_per_launch():
+    p = os.path.join(ROOT, "profiles", "step_f32_ring_stack.txt")
+    try:
+        for ln in open(p):
+            if ln.startswith("dram_bytes_per_launch:"):
+                return float(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def _e2e(ctx, args, stream, dev):
+    import torch
+    views = ctx.state(0)
+    n = args.packs
+    host = {k: torch.empty(v[:n].shape, dtype=v.dtype, pin_memory=True) for k, v in views.items()}
+    torch.cuda.synchronize(dev)
+    for k, v in views.items():
+        host[k].copy_(v[:n])
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    step0 = ctx.tally(0)["step"]
+    K = max(2, args.steps // 2)
+    t0 = ctx.tally(0)["pack_steps"]
+    torch.cuda.synchronize(dev)
+    t_start = time.perf_counter()
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            for key, v in views.items():
+                v[:n].copy_(host[key], non_blocking=True)
+        ctx.resume(0, n, step0)
+        ctx.step(0, args.micro)
+        T = ctx.tally(0)  # D2H of the observables, synchronises
+    t_e2e = time.perf_counter() - t_start
+    # resume() zeroes the device counters: count the last call's pack-steps
+    per_call = T["pack_steps"]
+    d2h = 8 * (16 + 16 + 6) + 8 * (T["exit_hist"].size + T["r_hist"].size + T["ke_hist"].size +
+                                   T["teff_hist"].size + T["loss_map"].size)
+    return {"value": per_call * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "note": "pinned host pack state -> device, micro steps, "
+                                                     "tally -> host, every step"}
+
+
+def _fp64(args, w32, local, stream, dev):
+    import torch
+    from paper_2609_31258_b300 import mucite, workloads as W
+    w = W.ring_stack(n_packs=args.packs, n_steps=0, seed=w32.run.seed, precision=1)
+    ctx = mucite.Context(local, stream)
+    mucite.load_workload(ctx, w, 0)
+    micro = max(100, args.micro // 4)
+    for _ in range(2):
+        ctx.step(0, micro)
+    torch.cuda.synchronize(dev)
+    T0 = ctx.tally(0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.fp64_steps):
+        ctx.step(0, micro)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    T1 = ctx.tally(0)
+    ms = a.elapsed_time(b)
+    ps = T1["pack_steps"] - T0["pack_steps"]
+    ctx.close()
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "micro_steps_timed": micro * args.fp64_steps,
+            "ms": ms, "note": "one launch per micro step, FP64 state and fields"}
+
+
+if __name__ == "__main__":
+    main()

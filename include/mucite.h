@@ -1,0 +1,240 @@
+/*
+ * mucite.h -- C ABI of the B300 (sm_103a) ion-pack step library.
+ *
+ * The library advances weighted ion packs through baked axisymmetric (r,z)
+ * fields, in the operator order of the paper's runtime (Methods, "Simulation
+ * scope and modular architecture"): per micro step, gather gas and fields at
+ * the ion -> ion-gas collisions (Eq. 6, IICT paragraph) -> leapfrog kick and
+ * drift under E_DC + E_RF(t) + E_SCE (Eq. 3, Eq. 4) -> terminal
+ * classification ("Terminal events"); per macro step, CIC deposit ->
+ * cylindrical Poisson -> E_SCE ("Axisymmetric PIC space charge update").
+ *
+ * Conventions (all calls):
+ *  - Every call returns a mucite_status (0 = MUCITE_OK, < 0 = error) and
+ *    never throws or aborts; mucite_last_error() describes the last failure.
+ *  - Host pointers passed in are read during the call and copied; the caller
+ *    keeps ownership. Device pointers (the pack pool) stay owned by the
+ *    caller and must outlive their instance.
+ *  - Work is enqueued on the context's CUDA stream; only mucite_tally,
+ *    mucite_pic_read and mucite_sync wait for it.
+ *  - Node arrays are row-major [Nz][Nr]; node counts include both ends
+ *    (Supporting Information Table S2: 2001 nodes for 20 mm at 0.01 mm).
+ *  - SI units. Internal energy is stored as E_int / k_B (kelvin units).
+ *  - Positions of the FP32 path live on a fixed-point lattice:
+ *    x = xq * R * 2^-30, y = yq * R * 2^-30, z = z0 + zq * (z1 - z0) * 2^-30
+ *    (int32). Every discrete decision (mask lookup, classification, deposit,
+ *    tally bins) is taken on this lattice; the FP64 path quantises its FP64
+ *    positions as rint(x * 2^30 / R), rint((z - z0) * 2^30 / (z1 - z0)).
+ */
+#ifndef MUCITE_H
+#define MUCITE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mucite_ctx mucite_ctx;
+typedef int mucite_status;
+
+enum {
+    MUCITE_OK = 0,
+    MUCITE_E_ARG = -1,      /* invalid argument or size */
+    MUCITE_E_OOM = -2,      /* device allocation failed */
+    MUCITE_E_CUDA = -3,     /* a CUDA call or kernel launch failed */
+    MUCITE_E_OVERFLOW = -4, /* fixed-point charge bound exceeded (sum |q W| >= 2^33) */
+    MUCITE_E_STATE = -5,    /* call out of order (no fields, no instance, ...) */
+    MUCITE_E_TIMEOUT = -6   /* a bounded device wait gave up */
+};
+
+enum { MUCITE_FP32 = 0, MUCITE_FP64 = 1 };
+
+/* Pack status byte: terminal classes of "Terminal events, snapshots, and
+ * reported observables". A terminal pack is never re-activated. */
+enum {
+    MUCITE_ACTIVE = 0,
+    MUCITE_TRANSMITTED = 1,
+    MUCITE_ELECTRODE = 2,
+    MUCITE_RADIAL = 3,
+    MUCITE_AXIAL = 4,
+    MUCITE_EMPTY = 255
+};
+
+#define MUCITE_MAX_INSTANCES 256
+
+/* Axisymmetric grid: nr x nz nodes over r in [0, R], z in [z0, z1]. */
+typedef struct {
+    int32_t nr, nz;
+    double R, z0, z1;
+} mucite_grid;
+
+/* Ion template (Methods, "Simulation scope": mass, charge state, collision
+ * cross section, atom count, heat-capacity profile). Heat capacity
+ * Cv / k_B = 3 n_atoms * min(1, cv_c0 + cv_c1 * T); classical: (1, 0). */
+typedef struct {
+    double mass_da;
+    int32_t charge;
+    double ccs_m2;
+    double n_atoms;
+    double cv_c0, cv_c1;
+    double T_init; /* initial T_eff */
+} mucite_ion_template;
+
+/* Source definition ("Continuous current Gaussian source", Eq. 5).
+ * profile 0: uniform over the disc r <= radius; 1: Gaussian of width sigma
+ * truncated at radius. n_initial packs are placed at once (on z_plane, or
+ * uniformly in [prefill_z0, prefill_z1) when that range is non-empty); a
+ * non-zero current_A then releases packs of weight W through the Eq. 5
+ * accumulator at the start of every mucite_step call. */
+typedef struct {
+    int32_t profile;
+    double z_plane, radius, sigma, T_vel;
+    int32_t half_space; /* fold v_z to >= 0 */
+    int64_t n_initial;
+    double prefill_z0, prefill_z1;
+    double current_A;
+    int64_t weight;
+} mucite_source;
+
+/* Operating conditions and run settings of one instance. v_rf is the peak
+ * voltage applied to the RF basis (V_ref = 1 V, Eq. 4); dc_scale multiplies
+ * the DC basis; p_scale multiplies the gas pressure. Histogram layout of the
+ * tallies is fixed here. */
+typedef struct {
+    double dt, v_rf, f_rf, phi_rf, dc_scale, p_scale;
+    double hit_dist, z_exit, r_det, m_gas_da;
+    uint64_t seed;
+    int32_t precision;    /* MUCITE_FP32 (fused) or MUCITE_FP64 (plain) */
+    int32_t pic_interval; /* steps between space-charge updates, 0 = none */
+    int32_t exit_bin_steps, n_exit_bins, n_r_bins, n_ke_bins, n_teff_bins, n_loss_r, n_loss_z;
+    double ke_max_ev, teff_max;
+} mucite_run;
+
+/* Byte offsets of the structure-of-arrays pack pool (each array 256-byte
+ * aligned). FP32: xq, yq, zq int32; vx, vy, vz, eint float. FP64: x, y, z,
+ * vx, vy, vz, eint double. Both: status uint8, t_term int32 (step count at
+ * which the pack became terminal, -1 while active). */
+typedef struct {
+    int64_t off_x, off_y, off_z, off_vx, off_vy, off_vz, off_eint, off_status, off_t_term;
+    int64_t total_bytes;
+    int32_t pos_bytes, vel_bytes;
+} mucite_layout;
+
+/* Observables of one instance (Eq. 8; "reported observables"; conservation
+ * of represented weight). Arrays are caller-owned host buffers sized by the
+ * instance's run settings; a NULL array is skipped. */
+typedef struct {
+    int64_t count[8], weight[8];      /* by status code (index 0..4) */
+    double sum_w_ke[8], sum_w_teff[8];/* sum of W * KE [eV] and W * T_eff [K] by status */
+    int64_t emitted_count, emitted_weight;
+    int64_t pack_steps;               /* active pack-steps advanced so far */
+    int64_t collisions;               /* accepted collision events so far */
+    int64_t candidate_overflow;       /* steps that hit the per-step candidate cap */
+    int64_t step;                     /* instance clock (steps taken) */
+    int64_t *exit_hist;               /* [n_exit_bins] transmitted W by t_term / exit_bin_steps */
+    int64_t *r_hist;                  /* [n_r_bins] transmitted W by exit radius over [0, r_det] */
+    int64_t *ke_hist;                 /* [n_ke_bins] transmitted W by KE over [0, ke_max_ev] */
+    int64_t *teff_hist;               /* [n_teff_bins] transmitted W by T_eff over [0, teff_max] */
+    int64_t *loss_map;                /* [n_loss_z][n_loss_r] electrode-hit W over the domain */
+} mucite_tally_out;
+
+/* Context on one device; `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream), e.g. torch.cuda.current_stream().cuda_stream. */
+mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream);
+void mucite_destroy(mucite_ctx *ctx);
+/* Text of the last error on this context (or of a failed create when ctx is
+ * NULL); valid until the next call on the context. */
+const char *mucite_last_error(const mucite_ctx *ctx);
+
+/* Load the baked static fields (Methods, "Coordinate system, static fields,
+ * and RF convention"; "Gas field and electrode mask coupling").
+ * phi_dc, phi_rf_basis: FP64 potentials [Nz][Nr] (RF basis: adjacent RF
+ * electrodes at +1/-1 V); E = -grad(phi) is formed on the device by central
+ * differences (one-sided at the domain edges, E_r = 0 on the axis).
+ * gas_p [Pa], gas_T [K], gas_ur, gas_uz [m/s]: FP64 [Nz][Nr].
+ * metal_mask: uint8 [Nz][Nr], 1 = metal node; surf_dist: FP64 [Nz][Nr]
+ * distance to the metal surface [m].
+ * pic: PIC grid for the space-charge field, or NULL for none; it must span
+ * the same (r, z) box as `g`.
+ * Errors: MUCITE_E_ARG (NULL arrays, nr < 2 or nz < 2, bad box),
+ * MUCITE_E_STATE (instances already injected), MUCITE_E_OOM, MUCITE_E_CUDA. */
+mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const double *phi_dc,
+                                 const double *phi_rf_basis, const double *gas_p,
+                                 const double *gas_T, const double *gas_ur, const double *gas_uz,
+                                 const uint8_t *metal_mask, const double *surf_dist,
+                                 const mucite_grid *pic);
+
+/* Layout of a pack pool of `capacity` packs in the given precision. */
+mucite_status mucite_state_layout(int precision, int64_t capacity, mucite_layout *out);
+
+/* Create (or replace) instance `instance` in [0, MUCITE_MAX_INSTANCES):
+ * binds the caller's device pool `d_state` (layout from
+ * mucite_state_layout, 256-byte aligned, owned by the caller), marks all
+ * slots empty, and places src->n_initial packs (source sampling of
+ * "Continuous current Gaussian source"; Maxwellian velocities at T_vel;
+ * E_int = E_int(T_init)). Random draws: Philox4x32-10 keyed by run->seed,
+ * counter (pack id, 0, block, 1).
+ * Errors: MUCITE_E_ARG (sizes, NULL pool, misaligned pool, n_initial >
+ * capacity, bad histogram sizes), MUCITE_E_OVERFLOW (capacity * |q| * W >=
+ * 2^33 with space charge on), MUCITE_E_STATE (no fields loaded), MUCITE_E_OOM. */
+mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_template *ion,
+                            const mucite_source *src, const mucite_run *run, void *d_state,
+                            int64_t capacity);
+
+/* Free the instance's device buffers (the caller's pool is not touched). */
+mucite_status mucite_release(mucite_ctx *ctx, int instance);
+
+/* Declare that the caller has written `n_slots` packs into the instance's
+ * pool (checkpoint import, or a state prepared by a test) and set the
+ * instance clock to `step`; counters restart at zero.
+ * Errors: MUCITE_E_ARG (n_slots > capacity, step < 0), MUCITE_E_STATE. */
+mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int64_t step);
+
+/* Advance `n_steps` micro steps of instance `instance`, or of every FP32
+ * instance in one batched launch per chunk plus every FP64 instance when
+ * instance = -1. With space charge on, a PIC update runs whenever the
+ * instance clock is a multiple of pic_interval before the next micro step.
+ * Per micro step and active pack: gather -> collisions -> kick -> drift ->
+ * classify. Random draws: counter (pack id, step, 3k + b, 0) for candidate k.
+ * Errors: MUCITE_E_ARG (n_steps < 0), MUCITE_E_STATE, MUCITE_E_CUDA. */
+mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps);
+
+/* Space-charge macro step of one instance: int64 CIC deposit of q*W in units
+ * of e * 2^-30 -> finite-volume cylindrical Poisson (dPhi/dr = 0 on the
+ * axis, Phi = 0 at both axial ends and at r = R) solved by an FP32 DST-I in z
+ * with a tridiagonal solve per mode, refined in FP64 until
+ * ||b - A Phi|| / ||b|| <= 1e-6 (at most 8 refinements, warm-started from
+ * the previous solution) -> E_SCE by central differences on the PIC grid.
+ * Errors: MUCITE_E_STATE (no PIC grid or instance), MUCITE_E_CUDA. */
+mucite_status mucite_pic_update(mucite_ctx *ctx, int instance);
+
+/* Observables of the instance computed from its pack pool (synchronises the
+ * stream). Integer counts and histograms are exact; FP64 sums are
+ * accumulated with atomics (order-dependent in the last bits). */
+mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out);
+
+/* Copy the instance's last space-charge solution to host buffers (any may be
+ * NULL): Q int64 [pNz][pNr] (units e * 2^-30), phi FP64 [pNz][pNr],
+ * E_r and E_z float [pNz][pNr], and the final relative residual.
+ * Synchronises the stream. */
+mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double *phi, float *er,
+                              float *ez, double *rel_residual);
+
+/* Launch shape of the fused FP32 step: at most `steps_per_launch` micro
+ * steps are fused per launch (state stays in registers between them) with
+ * `threads_per_block` threads (a multiple of 32, <= 1024). 0 keeps the
+ * current value. */
+mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block);
+
+/* Number of kernels this context has launched since creation. */
+int64_t mucite_launch_count(const mucite_ctx *ctx);
+
+/* Wait for all work enqueued on the context's stream. */
+mucite_status mucite_sync(mucite_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MUCITE_H */

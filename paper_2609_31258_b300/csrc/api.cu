@@ -1,0 +1,968 @@
+// Host side of the C ABI declared in include/mucite.h: context, field
+// loading, instances (pack pools owned by the caller), stepping with the
+// space-charge macro step interleaved, tallies. All device work is enqueued
+// on the context stream; calls return a status and never throw.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pic.cuh"
+
+using namespace mucite;
+
+namespace {
+
+struct Instance {
+    bool used = false;
+    mucite_ion_template ion{};
+    mucite_source src{};
+    mucite_run run{};
+    void *pool = nullptr;
+    int64_t capacity = 0;
+    mucite_layout lay{};
+    int64_t n_slots = 0;
+    int64_t step = 0;
+    double src_acc = 0.0;
+    unsigned long long *d_counters = nullptr; // [3]
+    // tally buffers: [0..7] count, [8..15] wsum, then hist arrays; sums in d_tsum
+    unsigned long long *d_tally = nullptr;
+    double *d_tsum = nullptr; // [16]: sum_ke[8], sum_teff[8]
+    int64_t tally_len = 0;
+    bool has_pic = false;
+    PicInst pic{};
+    InstF32 f32{};
+    InstF64 f64{};
+};
+
+} // namespace
+
+struct mucite_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool fields = false;
+    mucite_grid g{};
+    NodeF *d_node = nullptr;
+    float *d_dmask = nullptr;
+    double *d_f64[8] = {};
+    bool has_pic_grid = false;
+    mucite_grid pg_grid{};
+    PicGeom pg{};
+    float *d_S = nullptr, *d_cp = nullptr, *d_invm = nullptr, *d_lo = nullptr;
+    double *d_a = nullptr, *d_c = nullptr, *d_A = nullptr;
+    Instance inst[MUCITE_MAX_INSTANCES];
+    InstF32 *d_insts = nullptr;
+    int32_t *d_tiles = nullptr;
+    PicInst *d_picinst = nullptr;
+    int steps_per_launch = 256;
+    int threads = 256;
+    int64_t launches = 0;
+};
+
+namespace {
+
+std::string g_create_err;
+
+mucite_status fail(mucite_ctx *ctx, mucite_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_err = buf;
+    return st;
+}
+
+struct DevGuard {
+    int prev = -1, want;
+    explicit DevGuard(int d) : want(d)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MUCITE_E_OOM : MUCITE_E_CUDA,     \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+#define CKL()                                                                                    \
+    do {                                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                                     \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, MUCITE_E_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T> void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
+
+void layout_of(int precision, int64_t cap, mucite_layout *L)
+{
+    const int pb = precision == MUCITE_FP64 ? 8 : 4, vb = pb;
+    int64_t off = 0;
+    auto put = [&](int64_t &o, int64_t bytes) {
+        o = off;
+        off += align256(bytes);
+    };
+    put(L->off_x, cap * pb);
+    put(L->off_y, cap * pb);
+    put(L->off_z, cap * pb);
+    put(L->off_vx, cap * vb);
+    put(L->off_vy, cap * vb);
+    put(L->off_vz, cap * vb);
+    put(L->off_eint, cap * vb);
+    put(L->off_status, cap);
+    put(L->off_t_term, cap * 4);
+    L->total_bytes = off;
+    L->pos_bytes = pb;
+    L->vel_bytes = vb;
+}
+
+Profile profile_of(const mucite_ion_template &ion)
+{
+    Profile p;
+    p.n3 = 3.0 * ion.n_atoms;
+    p.c0 = ion.cv_c0;
+    p.c1 = ion.cv_c1;
+    if (ion.cv_c1 > 0.0) {
+        p.tcap = (1.0 - ion.cv_c0) / ion.cv_c1;
+        p.ecap = ion.cv_c0 * p.tcap + 0.5 * ion.cv_c1 * p.tcap * p.tcap;
+    } else {
+        p.tcap = INFINITY;
+        p.ecap = INFINITY;
+    }
+    return p;
+}
+
+double eint_of_T(const Profile &p, double T)
+{
+    if (T <= p.tcap) return p.n3 * (p.c0 * T + 0.5 * p.c1 * T * T);
+    return p.n3 * (p.ecap + (T - p.tcap));
+}
+
+void free_instance(Instance &I)
+{
+    dfree(I.d_counters);
+    dfree(I.d_tally);
+    dfree(I.d_tsum);
+    dfree(I.pic.Q);
+    dfree(I.pic.phi);
+    dfree(I.pic.r32);
+    dfree(I.pic.hat);
+    dfree(I.pic.d32);
+    dfree(I.pic.esc);
+    dfree(I.pic.er64);
+    dfree(I.pic.ez64);
+    dfree(I.pic.red);
+    dfree(I.pic.conv);
+    I = Instance();
+}
+
+void free_fields(mucite_ctx *ctx)
+{
+    dfree(ctx->d_node);
+    dfree(ctx->d_dmask);
+    for (auto &p : ctx->d_f64) dfree(p);
+    dfree(ctx->d_S);
+    dfree(ctx->d_cp);
+    dfree(ctx->d_invm);
+    dfree(ctx->d_lo);
+    dfree(ctx->d_a);
+    dfree(ctx->d_c);
+    dfree(ctx->d_A);
+    ctx->fields = false;
+    ctx->has_pic_grid = false;
+}
+
+template <typename T> T *at(void *pool, int64_t off) { return (T *)((char *)pool + off); }
+
+void bind_params(mucite_ctx *ctx, Instance &I)
+{
+    const mucite_run &r = I.run;
+    const mucite_ion_template &ion = I.ion;
+    const mucite_grid &g = ctx->g;
+    const double M = ion.mass_da * kDa, mg = r.m_gas_da * kDa;
+    const double mu = M * mg / (M + mg);
+    const Profile pf = profile_of(ion);
+    const int64_t zexit_q = (int64_t)ceil((r.z_exit - g.z0) / (g.z1 - g.z0) * kLat);
+    const int64_t rdet_q = (int64_t)floor(r.r_det / g.R * kLat);
+    if (I.lay.pos_bytes == 4) {
+        InstF32 &P = I.f32;
+        P = InstF32{};
+        P.xq = at<int32_t>(I.pool, I.lay.off_x);
+        P.yq = at<int32_t>(I.pool, I.lay.off_y);
+        P.zq = at<int32_t>(I.pool, I.lay.off_z);
+        P.vx = at<float>(I.pool, I.lay.off_vx);
+        P.vy = at<float>(I.pool, I.lay.off_vy);
+        P.vz = at<float>(I.pool, I.lay.off_vz);
+        P.eint = at<float>(I.pool, I.lay.off_eint);
+        P.status = at<uint8_t>(I.pool, I.lay.off_status);
+        P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+        P.v_rf = r.v_rf;
+        P.dtf = r.dt * r.f_rf;
+        P.phi_rf = r.phi_rf;
+        P.kick = (float)(ion.charge * kE * r.dt / M);
+        P.dc_scale = (float)r.dc_scale;
+        P.cxs = (float)(r.dt * kLat / g.R);
+        P.czs = (float)(r.dt * kLat / (g.z1 - g.z0));
+        P.dt = (float)r.dt;
+        P.psig = (float)(r.p_scale * ion.ccs_m2 / kKB);
+        P.s_coef = (float)(2.0 * kKB / mg);
+        P.fM = (float)(M / (M + mg));
+        P.fm = (float)(mg / (M + mg));
+        P.mu_2kb = (float)(mu / (2.0 * kKB));
+        P.g_coef = (float)(2.0 * kKB / mu);
+        P.n3 = (float)pf.n3;
+        P.c0 = (float)pf.c0;
+        P.c1 = (float)pf.c1;
+        P.tcap = std::isinf(pf.tcap) ? 3.0e38f : (float)pf.tcap;
+        P.ecap = std::isinf(pf.ecap) ? 3.0e38f : (float)pf.ecap;
+        P.key0 = (uint32_t)r.seed;
+        P.key1 = (uint32_t)(r.seed >> 32);
+        P.zexit_q = zexit_q;
+        P.rdet2 = (uint64_t)(rdet_q * rdet_q);
+        P.hit = (float)r.hit_dist;
+        if (I.has_pic) {
+            P.esc = I.pic.esc;
+            P.pnr = ctx->pg.pnr;
+            P.pnz = ctx->pg.pnz;
+            P.psr = (float)(ctx->pg.pnr - 1) * (1.0f / 1073741824.0f);
+        }
+        P.counters = I.d_counters;
+    } else {
+        InstF64 &P = I.f64;
+        P = InstF64{};
+        P.x = at<double>(I.pool, I.lay.off_x);
+        P.y = at<double>(I.pool, I.lay.off_y);
+        P.z = at<double>(I.pool, I.lay.off_z);
+        P.vx = at<double>(I.pool, I.lay.off_vx);
+        P.vy = at<double>(I.pool, I.lay.off_vy);
+        P.vz = at<double>(I.pool, I.lay.off_vz);
+        P.eint = at<double>(I.pool, I.lay.off_eint);
+        P.status = at<uint8_t>(I.pool, I.lay.off_status);
+        P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+        P.qm = ion.charge * kE / (ion.mass_da * kDa);
+        P.dc_scale = r.dc_scale;
+        P.dt = r.dt;
+        P.p_scale = r.p_scale;
+        P.sigma = ion.ccs_m2;
+        P.M = M;
+        P.mg = mg;
+        P.prof = pf;
+        P.seed = r.seed;
+        P.zexit_q = zexit_q;
+        P.rdet_q = rdet_q;
+        P.hit = (float)r.hit_dist;
+        if (I.has_pic) {
+            P.er_sc = I.pic.er64;
+            P.ez_sc = I.pic.ez64;
+            P.pnr = ctx->pg.pnr;
+            P.pnz = ctx->pg.pnz;
+        }
+        P.counters = I.d_counters;
+    }
+}
+
+GridF32 grid_f32(const mucite_ctx *ctx)
+{
+    GridF32 G;
+    G.node = ctx->d_node;
+    G.dmask = ctx->d_dmask;
+    G.nr = ctx->g.nr;
+    G.nz = ctx->g.nz;
+    G.sr = (float)(ctx->g.nr - 1) * (1.0f / 1073741824.0f);
+    return G;
+}
+
+GridF64 grid_f64(const mucite_ctx *ctx)
+{
+    GridF64 G;
+    G.er_dc = ctx->d_f64[0];
+    G.ez_dc = ctx->d_f64[1];
+    G.er_rf = ctx->d_f64[2];
+    G.ez_rf = ctx->d_f64[3];
+    G.gas_p = ctx->d_f64[4];
+    G.gas_T = ctx->d_f64[5];
+    G.gas_ur = ctx->d_f64[6];
+    G.gas_uz = ctx->d_f64[7];
+    G.dmask = ctx->d_dmask;
+    G.nr = ctx->g.nr;
+    G.nz = ctx->g.nz;
+    G.R = ctx->g.R;
+    G.z0 = ctx->g.z0;
+    G.z1 = ctx->g.z1;
+    return G;
+}
+
+double rf_scalar(const mucite_run &r, int64_t n)
+{
+    if (r.v_rf == 0.0 || r.f_rf == 0.0) return 0.0;
+    const double x = (double)n * (r.dt * r.f_rf);
+    const double frac = x - floor(x);
+    return r.v_rf * cos(2.0 * kPi * frac + r.phi_rf);
+}
+
+mucite_status inject_packs(mucite_ctx *ctx, Instance &I, int64_t p0, int64_t count, bool prefill)
+{
+    if (count <= 0) return MUCITE_OK;
+    InjectArgs A{};
+    A.p0 = p0;
+    A.count = count;
+    A.profile = I.src.profile;
+    A.half_space = I.src.half_space;
+    A.prefill = prefill && I.src.prefill_z1 > I.src.prefill_z0;
+    A.z_plane = I.src.z_plane;
+    A.radius = I.src.radius;
+    A.sigma = I.src.sigma;
+    A.sd = sqrt(kKB * I.src.T_vel / (I.ion.mass_da * kDa));
+    A.pz0 = I.src.prefill_z0;
+    A.pz1 = I.src.prefill_z1;
+    A.e0 = eint_of_T(profile_of(I.ion), I.ion.T_init);
+    A.key0 = (uint32_t)I.run.seed;
+    A.key1 = (uint32_t)(I.run.seed >> 32);
+    A.precision = I.run.precision;
+    A.x = (char *)I.pool + I.lay.off_x;
+    A.y = (char *)I.pool + I.lay.off_y;
+    A.z = (char *)I.pool + I.lay.off_z;
+    A.vx = (char *)I.pool + I.lay.off_vx;
+    A.vy = (char *)I.pool + I.lay.off_vy;
+    A.vz = (char *)I.pool + I.lay.off_vz;
+    A.eint = (char *)I.pool + I.lay.off_eint;
+    A.status = at<uint8_t>(I.pool, I.lay.off_status);
+    A.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+    A.R = ctx->g.R;
+    A.gz0 = ctx->g.z0;
+    A.gz1 = ctx->g.z1;
+    launch_inject(A, ctx->stream);
+    ctx->launches++;
+    CKL();
+    return MUCITE_OK;
+}
+
+// Packs released by the continuous source over nsteps (Eq. 5): the
+// accumulator gains I dt / (z e) real ions per step and releases one pack
+// per W accumulated.
+int64_t source_emit(Instance &I, int64_t nsteps)
+{
+    if (!(I.src.current_A > 0.0) || I.src.weight <= 0) return 0;
+    const double per_step = I.src.current_A * I.run.dt / ((double)I.ion.charge * kE);
+    int64_t emitted = 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        I.src_acc += per_step;
+        while (I.src_acc >= (double)I.src.weight) {
+            I.src_acc -= (double)I.src.weight;
+            ++emitted;
+        }
+    }
+    return emitted;
+}
+
+mucite_status pic_update_one(mucite_ctx *ctx, Instance &I)
+{
+    const PicGeom &G = ctx->pg;
+    const size_t nn = (size_t)G.pnr * G.pnz;
+    CK(cudaMemsetAsync(I.pic.Q, 0, nn * sizeof(unsigned long long), ctx->stream));
+    DepositArgs D{};
+    D.precision = I.run.precision;
+    D.x = (char *)I.pool + I.lay.off_x;
+    D.y = (char *)I.pool + I.lay.off_y;
+    D.z = (char *)I.pool + I.lay.off_z;
+    D.status = at<uint8_t>(I.pool, I.lay.off_status);
+    D.n = I.n_slots;
+    D.sx = kLat / ctx->g.R;
+    D.sz = kLat / (ctx->g.z1 - ctx->g.z0);
+    D.gz0 = ctx->g.z0;
+    D.pnr = G.pnr;
+    D.pnz = G.pnz;
+    D.qw = (int64_t)I.ion.charge * I.src.weight;
+    D.Q = I.pic.Q;
+    launch_deposit(D, ctx->stream);
+    ctx->launches++;
+    CKL();
+    CK(cudaMemsetAsync(I.pic.red, 0, 4 * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(I.pic.conv, 0, sizeof(int), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_picinst, &I.pic, sizeof(PicInst), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->launches += launch_pic_solve(G, ctx->d_picinst, 1, 8, 1e-6, ctx->stream);
+    CKL();
+    return MUCITE_OK;
+}
+
+mucite_status check_instance(mucite_ctx *ctx, int instance)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (instance < 0 || instance >= MUCITE_MAX_INSTANCES)
+        return fail(ctx, MUCITE_E_ARG, "instance %d out of range", instance);
+    if (!ctx->inst[instance].used) return fail(ctx, MUCITE_E_STATE, "instance %d not injected", instance);
+    return MUCITE_OK;
+}
+
+// Advance a group of FP32 instances together by nsteps (one launch per chunk).
+mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int64_t nsteps)
+{
+    std::vector<InstF32> host(grp.size());
+    std::vector<int32_t> tiles(grp.size() + 1);
+    int64_t done = 0;
+    while (done < nsteps) {
+        int64_t chunk = std::min<int64_t>(nsteps - done, ctx->steps_per_launch);
+        for (Instance *I : grp) {
+            const int P = I->has_pic ? I->run.pic_interval : 0;
+            if (P > 0) {
+                if (I->step % P == 0) {
+                    const mucite_status st = pic_update_one(ctx, *I);
+                    if (st != MUCITE_OK) return st;
+                }
+                chunk = std::min<int64_t>(chunk, P - I->step % P);
+            }
+        }
+        int64_t total = 0;
+        for (size_t k = 0; k < grp.size(); ++k) {
+            Instance *I = grp[k];
+            host[k] = I->f32;
+            host[k].n_slots = I->n_slots;
+            host[k].step0 = I->step;
+            tiles[k] = (int32_t)total;
+            total += (I->n_slots + ctx->threads - 1) / ctx->threads;
+        }
+        tiles[grp.size()] = (int32_t)total;
+        if (total > 0) {
+            CK(cudaMemcpyAsync(ctx->d_insts, host.data(), sizeof(InstF32) * grp.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(int32_t) * (grp.size() + 1),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), (int)total,
+                            ctx->threads, (int)chunk, ctx->stream);
+            ctx->launches++;
+            CKL();
+        }
+        for (Instance *I : grp) I->step += chunk;
+        done += chunk;
+    }
+    return MUCITE_OK;
+}
+
+mucite_status step_f64_one(mucite_ctx *ctx, Instance &I, int64_t nsteps)
+{
+    const GridF64 G = grid_f64(ctx);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const int P = I.has_pic ? I.run.pic_interval : 0;
+        if (P > 0 && I.step % P == 0) {
+            const mucite_status st = pic_update_one(ctx, I);
+            if (st != MUCITE_OK) return st;
+        }
+        InstF64 p = I.f64;
+        p.n_slots = I.n_slots;
+        launch_step_f64(G, p, I.step, rf_scalar(I.run, I.step), ctx->stream);
+        ctx->launches++;
+        CKL();
+        I.step += 1;
+    }
+    return MUCITE_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return fail(nullptr, MUCITE_E_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, MUCITE_E_ARG, "no CUDA device %d", device);
+    mucite_ctx *ctx = new (std::nothrow) mucite_ctx();
+    if (!ctx) return fail(nullptr, MUCITE_E_OOM, "host allocation failed");
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DevGuard dg(device);
+    cudaError_t e = cudaMalloc(&ctx->d_insts, sizeof(InstF32) * MUCITE_MAX_INSTANCES);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_picinst, sizeof(PicInst) * MUCITE_MAX_INSTANCES);
+    if (e != cudaSuccess) {
+        fail(nullptr, MUCITE_E_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
+        dfree(ctx->d_insts);
+        dfree(ctx->d_tiles);
+        dfree(ctx->d_picinst);
+        delete ctx;
+        return MUCITE_E_OOM;
+    }
+    *out = ctx;
+    return MUCITE_OK;
+}
+
+void mucite_destroy(mucite_ctx *ctx)
+{
+    if (!ctx) return;
+    DevGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &I : ctx->inst)
+        if (I.used) free_instance(I);
+    free_fields(ctx);
+    dfree(ctx->d_insts);
+    dfree(ctx->d_tiles);
+    dfree(ctx->d_picinst);
+    delete ctx;
+}
+
+const char *mucite_last_error(const mucite_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+mucite_status mucite_state_layout(int precision, int64_t capacity, mucite_layout *out)
+{
+    if (!out || capacity < 0 || (precision != MUCITE_FP32 && precision != MUCITE_FP64))
+        return MUCITE_E_ARG;
+    layout_of(precision, capacity, out);
+    return MUCITE_OK;
+}
+
+mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const double *phi_dc,
+                                 const double *phi_rf_basis, const double *gas_p,
+                                 const double *gas_T, const double *gas_ur, const double *gas_uz,
+                                 const uint8_t *metal_mask, const double *surf_dist,
+                                 const mucite_grid *pic)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (!g || !phi_dc || !phi_rf_basis || !gas_p || !gas_T || !gas_ur || !gas_uz || !metal_mask ||
+        !surf_dist)
+        return fail(ctx, MUCITE_E_ARG, "NULL field array");
+    if (g->nr < 2 || g->nz < 2 || !(g->R > 0.0) || !(g->z1 > g->z0))
+        return fail(ctx, MUCITE_E_ARG, "bad grid (nr=%d nz=%d R=%g z0=%g z1=%g)", g->nr, g->nz, g->R,
+                    g->z0, g->z1);
+    if (pic && (pic->nr < 3 || pic->nz < 3 || pic->R != g->R || pic->z0 != g->z0 || pic->z1 != g->z1))
+        return fail(ctx, MUCITE_E_ARG, "PIC grid must have >= 3 nodes per axis and span the static box");
+    for (auto &I : ctx->inst)
+        if (I.used) return fail(ctx, MUCITE_E_STATE, "release all instances before reloading fields");
+    DevGuard dg(ctx->device);
+    free_fields(ctx);
+    const int64_t n = (int64_t)g->nr * g->nz;
+    if (n > (1LL << 31) / 2) return fail(ctx, MUCITE_E_ARG, "grid too large");
+    ctx->g = *g;
+    for (auto &p : ctx->d_f64) CK(cudaMalloc(&p, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_node, n * sizeof(NodeF)));
+    CK(cudaMalloc(&ctx->d_dmask, n * sizeof(float)));
+    double *d_phi = nullptr, *d_dist = nullptr;
+    uint8_t *d_mask = nullptr;
+    CK(cudaMalloc(&d_phi, 2 * n * sizeof(double)));
+    CK(cudaMalloc(&d_dist, n * sizeof(double)));
+    CK(cudaMalloc(&d_mask, n));
+    const size_t nb = n * sizeof(double);
+    CK(cudaMemcpyAsync(d_phi, phi_dc, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_phi + n, phi_rf_basis, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_f64[4], gas_p, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_f64[5], gas_T, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_f64[6], gas_ur, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_f64[7], gas_uz, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_dist, surf_dist, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_mask, metal_mask, n, cudaMemcpyHostToDevice, ctx->stream));
+    const double dr = g->R / (g->nr - 1), dz = (g->z1 - g->z0) / (g->nz - 1);
+    launch_efield(d_phi, g->nr, g->nz, dr, dz, ctx->d_f64[0], ctx->d_f64[1], ctx->stream);
+    launch_efield(d_phi + n, g->nr, g->nz, dr, dz, ctx->d_f64[2], ctx->d_f64[3], ctx->stream);
+    launch_pack_nodes(ctx->d_f64[0], ctx->d_f64[1], ctx->d_f64[2], ctx->d_f64[3], ctx->d_f64[4],
+                      ctx->d_f64[5], ctx->d_f64[6], ctx->d_f64[7], d_mask, d_dist, (int)n, ctx->d_node,
+                      ctx->d_dmask, ctx->stream);
+    ctx->launches += 3;
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_phi);
+    cudaFree(d_dist);
+    cudaFree(d_mask);
+    if (pic) {
+        PicGeom &G = ctx->pg;
+        G = PicGeom{};
+        G.pnr = pic->nr;
+        G.pnz = pic->nz;
+        G.M = pic->nz - 2;
+        G.Nu = pic->nr - 1;
+        G.dr = pic->R / (pic->nr - 1);
+        G.dz = (pic->z1 - pic->z0) / (pic->nz - 1);
+        G.bscale = -(kE / kLat) / (kEps0 * kPi * G.dz);
+        const int M = G.M, Nu = G.Nu;
+        std::vector<float> S((size_t)M * M), cp((size_t)Nu * M), invm((size_t)Nu * M), lo(Nu);
+        std::vector<double> a(Nu), c(Nu), A(Nu);
+        const double rz = (G.dr * G.dr) / (G.dz * G.dz);
+        for (int i = 0; i < Nu; ++i) {
+            if (i == 0) {
+                a[i] = 0.0;
+                c[i] = 1.0;
+                A[i] = rz / 4.0;
+            } else {
+                a[i] = 2.0 * (i - 0.5);
+                c[i] = 2.0 * (i + 0.5);
+                A[i] = 2.0 * i * rz;
+            }
+            lo[i] = (float)a[i];
+        }
+        const int64_t period = 2LL * (M + 1);
+        for (int j = 1; j <= M; ++j)
+            for (int k = 1; k <= M; ++k) {
+                const int64_t jk = ((int64_t)j * k) % period;
+                S[(size_t)(j - 1) * M + (k - 1)] = (float)sin(kPi * (double)jk / (double)(M + 1));
+            }
+        for (int k = 1; k <= M; ++k) {
+            const double s = sin(kPi * k / (2.0 * (M + 1)));
+            const double lam = 4.0 * s * s;
+            double cprev = 0.0;
+            for (int i = 0; i < Nu; ++i) {
+                const double d = -(a[i] + c[i] + A[i] * lam);
+                const double m = i == 0 ? d : d - a[i] * cprev;
+                const double cpi = c[i] / m;
+                cp[(size_t)i * M + (k - 1)] = (float)cpi;
+                invm[(size_t)i * M + (k - 1)] = (float)(1.0 / m);
+                cprev = cpi;
+            }
+        }
+        CK(cudaMalloc(&ctx->d_S, S.size() * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_cp, cp.size() * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_invm, invm.size() * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_lo, lo.size() * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_a, Nu * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_c, Nu * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_A, Nu * sizeof(double)));
+        CK(cudaMemcpy(ctx->d_S, S.data(), S.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_cp, cp.data(), cp.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_invm, invm.data(), invm.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_lo, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_a, a.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_c, c.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_A, A.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
+        G.S = ctx->d_S;
+        G.cp = ctx->d_cp;
+        G.invm = ctx->d_invm;
+        G.lo = ctx->d_lo;
+        G.a = ctx->d_a;
+        G.c = ctx->d_c;
+        G.A = ctx->d_A;
+        ctx->has_pic_grid = true;
+        ctx->pg_grid = *pic;
+    }
+    ctx->fields = true;
+    return MUCITE_OK;
+}
+
+mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_template *ion,
+                            const mucite_source *src, const mucite_run *run, void *d_state,
+                            int64_t capacity)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (instance < 0 || instance >= MUCITE_MAX_INSTANCES)
+        return fail(ctx, MUCITE_E_ARG, "instance %d out of range", instance);
+    if (!ctx->fields) return fail(ctx, MUCITE_E_STATE, "mucite_load_fields has not been called");
+    if (!ion || !src || !run || !d_state) return fail(ctx, MUCITE_E_ARG, "NULL argument");
+    if (((uintptr_t)d_state & 255) != 0) return fail(ctx, MUCITE_E_ARG, "pack pool not 256-byte aligned");
+    if (capacity < 0 || capacity > (1LL << 31) - 1024)
+        return fail(ctx, MUCITE_E_ARG, "capacity %lld out of range", (long long)capacity);
+    if (src->n_initial < 0 || src->n_initial > capacity)
+        return fail(ctx, MUCITE_E_ARG, "n_initial %lld exceeds capacity %lld", (long long)src->n_initial,
+                    (long long)capacity);
+    if (run->precision != MUCITE_FP32 && run->precision != MUCITE_FP64)
+        return fail(ctx, MUCITE_E_ARG, "bad precision");
+    if (!(run->dt > 0.0) || !(ion->mass_da > 0.0) || ion->charge == 0 || !(ion->n_atoms > 0.0) ||
+        src->weight <= 0 || run->m_gas_da <= 0.0)
+        return fail(ctx, MUCITE_E_ARG, "bad physical parameter (dt, mass, charge, atoms, weight)");
+    if (run->exit_bin_steps <= 0 || run->n_exit_bins <= 0 || run->n_r_bins <= 0 || run->n_ke_bins <= 0 ||
+        run->n_teff_bins <= 0 || run->n_loss_r <= 0 || run->n_loss_z <= 0 || !(run->ke_max_ev > 0.0) ||
+        !(run->teff_max > 0.0) || !(run->r_det > 0.0))
+        return fail(ctx, MUCITE_E_ARG, "bad tally layout");
+    if (src->profile == 1 && !(src->sigma > 0.0)) return fail(ctx, MUCITE_E_ARG, "Gaussian source needs sigma > 0");
+    const bool pic_on = ctx->has_pic_grid && run->pic_interval > 0;
+    if (run->pic_interval > 0 && !ctx->has_pic_grid)
+        return fail(ctx, MUCITE_E_STATE, "pic_interval > 0 but no PIC grid was loaded");
+    if (pic_on) {
+        const double bound = (double)capacity * std::fabs((double)ion->charge) * (double)src->weight;
+        if (bound >= 8589934592.0)
+            return fail(ctx, MUCITE_E_OVERFLOW, "capacity*|q|*W = %.3g >= 2^33 (fixed-point charge bound)",
+                        bound);
+    }
+    DevGuard dg(ctx->device);
+    Instance &I = ctx->inst[instance];
+    if (I.used) {
+        cudaStreamSynchronize(ctx->stream);
+        free_instance(I);
+    }
+    I.ion = *ion;
+    I.src = *src;
+    I.run = *run;
+    I.pool = d_state;
+    I.capacity = capacity;
+    layout_of(run->precision, capacity, &I.lay);
+    I.used = true;
+    CK(cudaMalloc(&I.d_counters, 3 * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(I.d_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    I.tally_len = 16 + run->n_exit_bins + run->n_r_bins + run->n_ke_bins + run->n_teff_bins +
+                  (int64_t)run->n_loss_r * run->n_loss_z;
+    CK(cudaMalloc(&I.d_tally, I.tally_len * sizeof(unsigned long long)));
+    CK(cudaMalloc(&I.d_tsum, 16 * sizeof(double)));
+    I.has_pic = pic_on;
+    if (pic_on) {
+        const PicGeom &G = ctx->pg;
+        const size_t nn = (size_t)G.pnr * G.pnz, nu = (size_t)G.M * G.Nu;
+        CK(cudaMalloc(&I.pic.Q, nn * sizeof(unsigned long long)));
+        CK(cudaMalloc(&I.pic.phi, nn * sizeof(double)));
+        CK(cudaMalloc(&I.pic.r32, nu * sizeof(float)));
+        CK(cudaMalloc(&I.pic.hat, nu * sizeof(float)));
+        CK(cudaMalloc(&I.pic.d32, nu * sizeof(float)));
+        CK(cudaMalloc(&I.pic.esc, nn * sizeof(float2)));
+        CK(cudaMalloc(&I.pic.red, 4 * sizeof(double)));
+        CK(cudaMalloc(&I.pic.conv, sizeof(int)));
+        CK(cudaMemsetAsync(I.pic.phi, 0, nn * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(I.pic.esc, 0, nn * sizeof(float2), ctx->stream));
+        CK(cudaMemsetAsync(I.pic.Q, 0, nn * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMemsetAsync(I.pic.red, 0, 4 * sizeof(double), ctx->stream));
+        if (run->precision == MUCITE_FP64) {
+            CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));
+            CK(cudaMalloc(&I.pic.ez64, nn * sizeof(double)));
+            CK(cudaMemsetAsync(I.pic.er64, 0, nn * sizeof(double), ctx->stream));
+            CK(cudaMemsetAsync(I.pic.ez64, 0, nn * sizeof(double), ctx->stream));
+        }
+    }
+    // every slot starts empty (status 255, t_term -1)
+    CK(cudaMemsetAsync((char *)d_state + I.lay.off_status, 0xFF, (size_t)capacity, ctx->stream));
+    CK(cudaMemsetAsync((char *)d_state + I.lay.off_t_term, 0xFF, (size_t)capacity * 4, ctx->stream));
+    bind_params(ctx, I);
+    I.n_slots = src->n_initial;
+    I.step = 0;
+    I.src_acc = 0.0;
+    return inject_packs(ctx, I, 0, src->n_initial, true);
+}
+
+mucite_status mucite_release(mucite_ctx *ctx, int instance)
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    DevGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_instance(ctx->inst[instance]);
+    return MUCITE_OK;
+}
+
+mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int64_t step)
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    Instance &I = ctx->inst[instance];
+    if (n_slots < 0 || n_slots > I.capacity || step < 0)
+        return fail(ctx, MUCITE_E_ARG, "n_slots %lld / step %lld out of range", (long long)n_slots,
+                    (long long)step);
+    DevGuard dg(ctx->device);
+    I.n_slots = n_slots;
+    I.step = step;
+    CK(cudaMemsetAsync(I.d_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    return MUCITE_OK;
+}
+
+mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (n_steps < 0) return fail(ctx, MUCITE_E_ARG, "n_steps < 0");
+    std::vector<Instance *> sel;
+    if (instance == -1) {
+        for (auto &I : ctx->inst)
+            if (I.used) sel.push_back(&I);
+    } else {
+        const mucite_status st = check_instance(ctx, instance);
+        if (st != MUCITE_OK) return st;
+        sel.push_back(&ctx->inst[instance]);
+    }
+    DevGuard dg(ctx->device);
+    // continuous source: release the packs accumulated over this call's steps
+    for (Instance *I : sel) {
+        const int64_t k = source_emit(*I, n_steps);
+        if (k > 0) {
+            if (I->n_slots + k > I->capacity)
+                return fail(ctx, MUCITE_E_ARG, "pack pool full (capacity %lld)", (long long)I->capacity);
+            const mucite_status st = inject_packs(ctx, *I, I->n_slots, k, false);
+            if (st != MUCITE_OK) return st;
+            I->n_slots += k;
+        }
+    }
+    std::vector<Instance *> f32;
+    for (Instance *I : sel) {
+        if (I->run.precision == MUCITE_FP32) {
+            f32.push_back(I);
+        } else {
+            const mucite_status st = step_f64_one(ctx, *I, n_steps);
+            if (st != MUCITE_OK) return st;
+        }
+    }
+    if (!f32.empty()) {
+        // instances advance together only while their PIC schedules agree
+        bool same = true;
+        for (Instance *I : f32)
+            same = same && I->run.pic_interval == f32[0]->run.pic_interval &&
+                   (!I->has_pic || I->step % I->run.pic_interval == f32[0]->step % I->run.pic_interval);
+        if (same) return step_f32_group(ctx, f32, n_steps);
+        for (Instance *I : f32) {
+            std::vector<Instance *> one{I};
+            const mucite_status st = step_f32_group(ctx, one, n_steps);
+            if (st != MUCITE_OK) return st;
+        }
+    }
+    return MUCITE_OK;
+}
+
+mucite_status mucite_pic_update(mucite_ctx *ctx, int instance)
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    Instance &I = ctx->inst[instance];
+    if (!I.has_pic) return fail(ctx, MUCITE_E_STATE, "instance %d has no space charge", instance);
+    DevGuard dg(ctx->device);
+    return pic_update_one(ctx, I);
+}
+
+mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
+{
+    mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    if (!out) return fail(ctx, MUCITE_E_ARG, "out is NULL");
+    Instance &I = ctx->inst[instance];
+    const mucite_run &r = I.run;
+    DevGuard dg(ctx->device);
+    CK(cudaMemsetAsync(I.d_tally, 0, I.tally_len * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(I.d_tsum, 0, 16 * sizeof(double), ctx->stream));
+    TallyArgs A{};
+    A.precision = r.precision;
+    A.x = (char *)I.pool + I.lay.off_x;
+    A.y = (char *)I.pool + I.lay.off_y;
+    A.z = (char *)I.pool + I.lay.off_z;
+    A.vx = (char *)I.pool + I.lay.off_vx;
+    A.vy = (char *)I.pool + I.lay.off_vy;
+    A.vz = (char *)I.pool + I.lay.off_vz;
+    A.eint = (char *)I.pool + I.lay.off_eint;
+    A.status = at<uint8_t>(I.pool, I.lay.off_status);
+    A.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+    A.n = I.n_slots;
+    A.sx = kLat / ctx->g.R;
+    A.sz = kLat / (ctx->g.z1 - ctx->g.z0);
+    A.gz0 = ctx->g.z0;
+    A.prof = profile_of(I.ion);
+    const double M = I.ion.mass_da * kDa;
+    A.c_ke = 0.5 * M / kE;
+    A.ke_scale = (double)r.n_ke_bins / r.ke_max_ev;
+    A.t_scale = (double)r.n_teff_bins / r.teff_max;
+    A.r_scale = (float)((double)r.n_r_bins / (r.r_det / ctx->g.R) / kLat);
+    A.lr_scale = (float)((double)r.n_loss_r / kLat);
+    A.exit_bin_steps = r.exit_bin_steps;
+    A.n_exit_bins = r.n_exit_bins;
+    A.n_r_bins = r.n_r_bins;
+    A.n_ke_bins = r.n_ke_bins;
+    A.n_teff_bins = r.n_teff_bins;
+    A.n_loss_r = r.n_loss_r;
+    A.n_loss_z = r.n_loss_z;
+    A.weight = I.src.weight;
+    A.count = I.d_tally;
+    A.wsum = I.d_tally + 8;
+    A.sum_ke = I.d_tsum;
+    A.sum_teff = I.d_tsum + 8;
+    A.exit_hist = I.d_tally + 16;
+    A.r_hist = A.exit_hist + r.n_exit_bins;
+    A.ke_hist = A.r_hist + r.n_r_bins;
+    A.teff_hist = A.ke_hist + r.n_ke_bins;
+    A.loss_map = A.teff_hist + r.n_teff_bins;
+    launch_tally(A, ctx->stream);
+    ctx->launches++;
+    CKL();
+    std::vector<unsigned long long> h(I.tally_len);
+    double sums[16];
+    unsigned long long cnt[3];
+    CK(cudaMemcpyAsync(h.data(), I.d_tally, I.tally_len * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(sums, I.d_tsum, sizeof sums, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(cnt, I.d_counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 8; ++k) {
+        out->count[k] = (int64_t)h[k];
+        out->weight[k] = (int64_t)h[8 + k];
+        out->sum_w_ke[k] = sums[k];
+        out->sum_w_teff[k] = sums[8 + k];
+    }
+    out->emitted_count = I.n_slots;
+    out->emitted_weight = I.n_slots * I.src.weight;
+    out->pack_steps = (int64_t)cnt[0];
+    out->collisions = (int64_t)cnt[1];
+    out->candidate_overflow = (int64_t)cnt[2];
+    out->step = I.step;
+    int64_t off = 16;
+    auto copy_out = [&](int64_t *dst, int64_t len) {
+        if (dst)
+            for (int64_t k = 0; k < len; ++k) dst[k] = (int64_t)h[off + k];
+        off += len;
+    };
+    copy_out(out->exit_hist, r.n_exit_bins);
+    copy_out(out->r_hist, r.n_r_bins);
+    copy_out(out->ke_hist, r.n_ke_bins);
+    copy_out(out->teff_hist, r.n_teff_bins);
+    copy_out(out->loss_map, (int64_t)r.n_loss_r * r.n_loss_z);
+    return MUCITE_OK;
+}
+
+mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double *phi, float *er,
+                              float *ez, double *rel_residual)
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    Instance &I = ctx->inst[instance];
+    if (!I.has_pic) return fail(ctx, MUCITE_E_STATE, "instance %d has no space charge", instance);
+    DevGuard dg(ctx->device);
+    const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
+    if (Q) CK(cudaMemcpyAsync(Q, I.pic.Q, nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, I.pic.phi, nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<float2> e;
+    if (er || ez) {
+        e.resize(nn);
+        CK(cudaMemcpyAsync(e.data(), I.pic.esc, nn * sizeof(float2), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    double red[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(red, I.pic.red, sizeof red, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < e.size(); ++k) {
+        if (er) er[k] = e[k].x;
+        if (ez) ez[k] = e[k].y;
+    }
+    if (rel_residual) *rel_residual = red[2];
+    return MUCITE_OK;
+}
+
+mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (steps_per_launch < 0 || steps_per_launch > 12000)
+        return fail(ctx, MUCITE_E_ARG, "steps_per_launch must be in [1, 12000]");
+    if (threads_per_block < 0 || threads_per_block % 32 != 0 || threads_per_block > 256)
+        return fail(ctx, MUCITE_E_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
+    if (steps_per_launch) ctx->steps_per_launch = steps_per_launch;
+    if (threads_per_block) ctx->threads = threads_per_block;
+    return MUCITE_OK;
+}
+
+int64_t mucite_launch_count(const mucite_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+mucite_status mucite_sync(mucite_ctx *ctx)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    DevGuard dg(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCITE_OK;
+}
+
+} // extern "C"

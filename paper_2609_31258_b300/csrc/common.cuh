@@ -1,0 +1,135 @@
+// Shared device-side definitions of the MuCITE B300 library: physical
+// constants, the Philox4x32-10 counter-based generator, the fixed-point
+// position lattice and the per-instance parameter blocks the kernels read.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mucite.h"
+
+namespace mucite {
+
+constexpr double kE = 1.602176634e-19;     // elementary charge [C]
+constexpr double kKB = 1.380649e-23;       // Boltzmann constant [J/K]
+constexpr double kDa = 1.66053906660e-27;  // dalton [kg]
+constexpr double kEps0 = 8.8541878128e-12; // vacuum permittivity [F/m]
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLat = 1073741824.0;      // 2^30 lattice units per R (r) or per (z1 - z0) (z)
+constexpr int kKmax = 32;                  // collision candidates examined per pack per step
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each taking
+// two 32x32 -> 64-bit products of counter words 0 and 2 with the round
+// multipliers, the key advanced by the two Weyl increments between rounds.
+// Counter = (pack id, step, draw block, purpose); key = (seed lo, seed hi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 23-bit uniform in (0,1): ((x >> 9) + 1/2) * 2^-23, exact in FP32 and FP64.
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+__device__ __forceinline__ double u01d(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+// Packed static-field node of the FP32 path: a = (Er_dc, Ez_dc, Er_rf, Ez_rf),
+// b = (p, T, u_r, u_z). One 32-byte sector per node.
+struct __align__(32) NodeF {
+    float4 a;
+    float4 b;
+};
+
+// Static grid as the FP32 step kernel sees it.
+struct GridF32 {
+    const NodeF *node;
+    const float *dmask; // -1 at metal nodes, else surface distance [m]
+    int nr, nz;
+    float sr;           // (nr - 1) * 2^-30: lattice r -> grid units
+};
+
+// Static grid of the plain FP64 path (structure of arrays, FP64).
+struct GridF64 {
+    const double *er_dc, *ez_dc, *er_rf, *ez_rf, *gas_p, *gas_T, *gas_ur, *gas_uz;
+    const float *dmask;
+    int nr, nz;
+    double R, z0, z1;
+};
+
+// Heat-capacity profile Cv/k_B = 3N min(1, c0 + c1 T): E_int(T) = 3N (c0 T +
+// c1 T^2 / 2) below Tcap = (1 - c0)/c1, linear above.
+struct Profile {
+    double n3, c0, c1, tcap, ecap; // ecap per 3N
+};
+
+// Per-instance parameters of the fused FP32 step (one entry per instance in
+// a device array; copied to shared memory by every block).
+struct InstF32 {
+    int32_t *xq, *yq, *zq;
+    float *vx, *vy, *vz, *eint;
+    uint8_t *status;
+    int32_t *t_term;
+    int64_t n_slots;
+    int64_t step0;
+    double v_rf, dtf, phi_rf;  // RF scalar V * cos(2 pi frac(n dt f) + phi), FP64
+    float kick;                // q e dt / m
+    float dc_scale;
+    float cxs, czs;            // dt * 2^30 / R, dt * 2^30 / (z1 - z0): velocity -> lattice step
+    float dt;
+    float psig;                // p_scale * sigma / k_B  (n sigma = psig * p / T)
+    float s_coef;              // 2 k_B / m_gas  (s^2 = s_coef * T)
+    float fM, fm;              // M/(M+m), m/(M+m)
+    float mu_2kb;              // mu / (2 k_B): relative KE in kelvin units
+    float g_coef;              // 2 k_B / mu
+    float n3, c0, c1, tcap, ecap;
+    uint32_t key0, key1;
+    int64_t zexit_q;           // first lattice z counted as crossed
+    uint64_t rdet2;            // (floor(r_det / R * 2^30))^2
+    float hit;                 // electrode-hit distance [m]
+    const float2 *esc;         // space-charge field (E_r, E_z) on the PIC grid or NULL
+    int pnr, pnz;
+    float psr;                 // (pnr - 1) * 2^-30
+    unsigned long long *counters; // [0] pack-steps, [1] collisions, [2] candidate-cap hits
+};
+
+// Per-instance parameters of the plain FP64 step.
+struct InstF64 {
+    double *x, *y, *z, *vx, *vy, *vz, *eint;
+    uint8_t *status;
+    int32_t *t_term;
+    int64_t n_slots;
+    double qm, dc_scale, dt, p_scale, sigma, M, mg, T_unused;
+    Profile prof;
+    uint64_t seed;
+    int64_t zexit_q, rdet_q;
+    float hit;
+    const double *er_sc, *ez_sc;  // space-charge field on the PIC grid (FP64) or NULL
+    int pnr, pnz;
+    unsigned long long *counters;
+};
+
+// Kernel launchers (defined in the .cu files, called from api.cu).
+void launch_efield(const double *phi, int nr, int nz, double dr, double dz, double *er, double *ez,
+                   cudaStream_t s);
+void launch_pack_nodes(const double *er_dc, const double *ez_dc, const double *er_rf,
+                       const double *ez_rf, const double *p, const double *T, const double *ur,
+                       const double *uz, const uint8_t *mask, const double *dist, int n,
+                       NodeF *node, float *dmask, cudaStream_t s);
+
+} // namespace mucite

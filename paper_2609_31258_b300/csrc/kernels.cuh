@@ -1,0 +1,43 @@
+// Argument blocks and launchers of the pack kernels (see the .cu files).
+#pragma once
+
+#include "common.cuh"
+
+namespace mucite {
+
+struct InjectArgs {
+    int64_t p0, count;
+    int profile, half_space, prefill;
+    double z_plane, radius, sigma, sd, pz0, pz1, e0;
+    uint32_t key0, key1;
+    int precision;
+    void *x, *y, *z, *vx, *vy, *vz, *eint;
+    uint8_t *status;
+    int32_t *t_term;
+    double R, gz0, gz1;
+};
+
+struct TallyArgs {
+    int precision;
+    const void *x, *y, *z, *vx, *vy, *vz, *eint;
+    const uint8_t *status;
+    const int32_t *t_term;
+    int64_t n;
+    double sx, sz, gz0;  // FP64-path quantisation to the lattice
+    Profile prof;
+    double c_ke, ke_scale, t_scale;
+    float r_scale, lr_scale;
+    int exit_bin_steps, n_exit_bins, n_r_bins, n_ke_bins, n_teff_bins, n_loss_r, n_loss_z;
+    int64_t weight;
+    unsigned long long *count, *wsum;  // [8]
+    double *sum_ke, *sum_teff;         // [8]
+    unsigned long long *exit_hist, *r_hist, *ke_hist, *teff_hist, *loss_map;
+};
+
+void launch_inject(const InjectArgs &A, cudaStream_t s);
+void launch_tally(const TallyArgs &A, cudaStream_t s);
+void launch_step_f32(const GridF32 &G, const InstF32 *d_insts, const int32_t *d_tile_start,
+                     int n_inst, int total_tiles, int threads, int nsteps, cudaStream_t s);
+void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, cudaStream_t s);
+
+} // namespace mucite

@@ -1,0 +1,313 @@
+// Space-charge macro step ("Axisymmetric PIC space charge update").
+//
+// 1. CIC deposit of q*W onto the (r, z) PIC nodes as int64 fixed point
+//    (units e * 2^-30). The deposit is defined on the position lattice:
+//    r = floor(sqrt(xq^2 + yq^2)) exactly, cell index and 15-bit fractions
+//    from integer products, so the node charges are exact and independent of
+//    the order of the atomic additions.
+// 2. Finite-volume cylindrical Poisson operator over annular control volumes
+//    (no flux through the axis, Phi = 0 at both axial ends and at r = R),
+//    divided through by pi dz:
+//      a_i Phi_{i-1} + c_i Phi_{i+1} - (a_i + c_i) Phi_i
+//        + A_i (Phi_{j+1} - 2 Phi_j + Phi_{j-1}) = -Q_ij / (eps0 pi dz)
+//    with a_i = 2(i - 1/2), c_i = 2(i + 1/2), A_i = 2 i dr^2/dz^2 for i >= 1
+//    and a_0 = 0, c_0 = 1, A_0 = dr^2 / (4 dz^2).
+// 3. Iterative refinement: residual r = b - A Phi in FP64; correction from
+//    an FP32 fast solve -- DST-I in z as a dense contraction with the sine
+//    matrix S_jk = sin(pi j k / (M + 1)), a tridiagonal (Thomas) solve in r
+//    per axial mode with eigenvalue 4 sin^2(pi k / (2 (M + 1))), inverse
+//    DST-I -- accumulated into FP64 Phi until ||r|| / ||b|| <= tol
+//    (tol = 1e-6, the paper's Poisson tolerance). Convergence is decided on
+//    the device, so the macro step needs no host round trip.
+// 4. E_SCE = -grad(Phi) by central differences on the PIC grid (one-sided at
+//    the edges, E_r = 0 on the axis).
+// blockIdx.z selects the instance in batched launches.
+#include "common.cuh"
+#include "pic.cuh"
+
+namespace mucite {
+
+namespace {
+
+__device__ __forceinline__ uint64_t isqrt_floor(uint64_t v)
+{
+    uint64_t r = (uint64_t)sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+__device__ __forceinline__ int32_t q32p(double v)
+{
+    const double r = rint(v);
+    if (r < -2147483648.0) return INT32_MIN;
+    if (r > 2147483647.0) return INT32_MAX;
+    return (int32_t)r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+} // namespace
+
+__global__ void __launch_bounds__(256) deposit_kernel(DepositArgs A)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.n || A.status[p] != MUCITE_ACTIVE) return;
+    int32_t xq, yq, zq;
+    if (A.precision == MUCITE_FP32) {
+        xq = ((const int32_t *)A.x)[p];
+        yq = ((const int32_t *)A.y)[p];
+        zq = ((const int32_t *)A.z)[p];
+    } else {
+        xq = q32p(__dmul_rn(((const double *)A.x)[p], A.sx));
+        yq = q32p(__dmul_rn(((const double *)A.y)[p], A.sx));
+        zq = q32p(__dmul_rn(__dsub_rn(((const double *)A.z)[p], A.gz0), A.sz));
+    }
+    const uint64_t r2 = (uint64_t)((int64_t)xq * xq) + (uint64_t)((int64_t)yq * yq);
+    const uint64_t r = isqrt_floor(r2);
+    if (r >= (1ULL << 30) || zq < 0 || zq > (1 << 30)) return;
+    const uint64_t tr = r * (uint64_t)(A.pnr - 1);
+    const uint64_t tz = (uint64_t)zq * (uint64_t)(A.pnz - 1);
+    int64_t i = (int64_t)(tr >> 30), j = (int64_t)(tz >> 30);
+    int64_t fr = (int64_t)((tr & ((1ULL << 30) - 1)) >> 15);
+    int64_t fz = (int64_t)((tz & ((1ULL << 30) - 1)) >> 15);
+    if (i > A.pnr - 2) { i = A.pnr - 2; fr = 1 << 15; }
+    if (j > A.pnz - 2) { j = A.pnz - 2; fz = 1 << 15; }
+    const int64_t wr0 = (1 << 15) - fr, wr1 = fr, wz0 = (1 << 15) - fz, wz1 = fz;
+    unsigned long long *Q = A.Q + (size_t)j * A.pnr + i;
+    atomicAdd(Q, (unsigned long long)(A.qw * wr0 * wz0));
+    atomicAdd(Q + 1, (unsigned long long)(A.qw * wr1 * wz0));
+    atomicAdd(Q + A.pnr, (unsigned long long)(A.qw * wr0 * wz1));
+    atomicAdd(Q + A.pnr + 1, (unsigned long long)(A.qw * wr1 * wz1));
+}
+
+// ||b||^2 over the unknowns; also clears the convergence flag and counters.
+__global__ void __launch_bounds__(256) bnorm_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
+        acc += b * b;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&I.red[0], acc);
+}
+
+// r = b - A Phi (FP64) on the unknowns; r32 = (float) r; ||r||^2 into red[1].
+__global__ void __launch_bounds__(256) residual_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        const double *ph = I.phi + (size_t)j * G.pnr + i;
+        const double c = ph[0];
+        const double w = i > 0 ? ph[-1] : 0.0;
+        const double east = ph[1]; // i + 1 <= pnr - 1, Phi = 0 there
+        const double ax = G.a[i] * w + G.c[i] * east - (G.a[i] + G.c[i]) * c +
+                          G.A[i] * (ph[G.pnr] - 2.0 * c + ph[-G.pnr]);
+        const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
+        const double r = b - ax;
+        I.r32[e] = (float)r;
+        acc += r * r;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&I.red[1], acc);
+}
+
+// Convergence decision: red[2] = ||r|| / ||b||; conv when <= tol.
+__global__ void check_kernel(const PicInst *insts, double tol)
+{
+    const PicInst &I = insts[blockIdx.x];
+    if (threadIdx.x != 0 || *I.conv) return;
+    const double bb = I.red[0], rr = I.red[1];
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    I.red[2] = rel;
+    I.red[1] = 0.0;
+    if (rel <= tol) *I.conv = 1;
+    else I.red[3] += 1.0;
+}
+
+// Tiled FP32 contraction C(m, n) = alpha * sum_k A(m, k) B(k, n) with strided
+// operands; 64 x 64 tile, 16-deep k slices, 4 x 4 outputs per thread.
+template <bool A_M_CONTIG, bool B_N_CONTIG>
+__global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const float *A = g.a_is_S ? g.S : (g.a_sel == 0 ? I.r32 : I.hat);
+    const float *B = g.b_is_S ? g.S : (g.b_sel == 0 ? I.r32 : I.hat);
+    float *C = g.c_sel == 1 ? I.hat : I.d32;
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + 256 * r;
+            int mm, kk;
+            if (A_M_CONTIG) { mm = e & 63; kk = e >> 6; }
+            else { kk = e & 15; mm = e >> 4; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < g.Mo && gk < g.K) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
+            int nn;
+            if (B_N_CONTIG) { nn = e & 63; kk = e >> 6; }
+            else { kk = e & 15; nn = e >> 4; }
+            const int gn = n0 + nn;
+            const int gk2 = k0 + kk;
+            Bs[kk][nn] = (gn < g.No && gk2 < g.K) ? B[(size_t)gk2 * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][ty * 4 + u];
+                b[u] = Bs[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int gm = m0 + ty * 4 + u;
+        if (gm >= g.Mo) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gn = n0 + tx * 4 + v;
+            if (gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * acc[u][v];
+        }
+    }
+}
+
+// Tridiagonal solve per axial mode k, in place on hat[i][k] (i = 0..Nu-1),
+// with the elimination factors of the fixed operator precomputed.
+__global__ void __launch_bounds__(256) thomas_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.M) return;
+    float *h = I.hat + k;
+    float y = h[0] * G.invm[k];
+    h[0] = y;
+    for (int i = 1; i < G.Nu; ++i) {
+        y = (h[(size_t)i * G.M] - G.lo[i] * y) * G.invm[(size_t)i * G.M + k];
+        h[(size_t)i * G.M] = y;
+    }
+    float x = y;
+    for (int i = G.Nu - 2; i >= 0; --i) {
+        x = h[(size_t)i * G.M] - G.cp[(size_t)i * G.M + k] * x;
+        h[(size_t)i * G.M] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) update_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int64_t n = (int64_t)G.M * G.Nu;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        I.phi[(size_t)j * G.pnr + i] += (double)I.d32[e];
+    }
+}
+
+__global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.z];
+    const int64_t n = (int64_t)G.pnr * G.pnz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % G.pnr), j = (int)(e / G.pnr);
+        const double *ph = I.phi + e;
+        double dpr, dpz;
+        if (i == 0) dpr = 0.0;
+        else if (i == G.pnr - 1) dpr = (ph[0] - ph[-1]) / G.dr;
+        else dpr = (ph[1] - ph[-1]) / (2.0 * G.dr);
+        if (j == 0) dpz = (ph[G.pnr] - ph[0]) / G.dz;
+        else if (j == G.pnz - 1) dpz = (ph[0] - ph[-G.pnr]) / G.dz;
+        else dpz = (ph[G.pnr] - ph[-G.pnr]) / (2.0 * G.dz);
+        I.esc[e] = make_float2((float)-dpr, (float)-dpz);
+        if (I.er64) {
+            I.er64[e] = -dpr;
+            I.ez64[e] = -dpz;
+        }
+    }
+}
+
+void launch_deposit(const DepositArgs &A, cudaStream_t s)
+{
+    if (A.n <= 0) return;
+    deposit_kernel<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+}
+
+int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
+                     cudaStream_t s)
+{
+    int launches = 0;
+    const int64_t nu = (int64_t)G.M * G.Nu;
+    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
+    bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    ++launches;
+    DstGemm fwd{}, inv{};
+    // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
+    fwd.S = G.S; fwd.a_is_S = 0; fwd.a_sel = 0; fwd.b_is_S = 1; fwd.c_sel = 1;
+    fwd.Mo = G.Nu; fwd.No = G.M; fwd.K = G.M;
+    fwd.a_sm = 1; fwd.a_sk = G.Nu; fwd.b_sk = G.M; fwd.b_sn = 1; fwd.c_sm = G.M; fwd.c_sn = 1;
+    fwd.alpha = (float)(2.0 / (G.M + 1));
+    // d32[j][i] = sum_k S[j][k] hat[i][k]
+    inv.S = G.S; inv.a_is_S = 1; inv.b_is_S = 0; inv.b_sel = 1; inv.c_sel = 2;
+    inv.Mo = G.M; inv.No = G.Nu; inv.K = G.M;
+    inv.a_sm = G.M; inv.a_sk = 1; inv.b_sk = 1; inv.b_sn = G.M; inv.c_sm = G.Nu; inv.c_sn = 1;
+    inv.alpha = 1.0f;
+    const dim3 gf((G.M + 63) / 64, (G.Nu + 63) / 64, n_inst);
+    const dim3 gi((G.Nu + 63) / 64, (G.M + 63) / 64, n_inst);
+    for (int it = 0; it <= max_refine; ++it) {
+        residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);
+        launches += 2;
+        if (it == max_refine) break;
+        dst_gemm_kernel<true, true><<<gf, 256, 0, s>>>(fwd, d_insts);
+        thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        dst_gemm_kernel<false, false><<<gi, 256, 0, s>>>(inv, d_insts);
+        update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        launches += 4;
+    }
+    const int64_t nn = (int64_t)G.pnr * G.pnz;
+    esc_kernel<<<dim3((unsigned)std::min<int64_t>((nn + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(
+        G, d_insts);
+    return launches + 1;
+}
+
+} // namespace mucite

@@ -1,0 +1,314 @@
+// Fused FP32 ion-pack step: one thread per pack, up to K micro steps per
+// launch with the pack state held in registers.
+//
+// Per micro step n and active pack (operator order of the paper's runtime,
+// Methods "Simulation scope and modular architecture"):
+//   1. gather at x_n: bilinear E_DC, E_RF basis, gas (p, T, u_r, u_z) from the
+//      static grid, E_SCE from the PIC grid; E_r and u_r projected onto x, y
+//      (Eq. 3, zero on the axis);
+//   2. collisions (Eq. 6 and the IICT paragraph): null-collision sub-cycling
+//      with the Maxwellian gas partner, hard-sphere isotropic scattering and
+//      Borgnakke-Larsen internal exchange;
+//   3. kick v += (q/m)(s_dc E_DC + s_rf(n) E_RF + E_SCE) dt, s_rf from Eq. 4
+//      with the phase taken in FP64 once per (instance, step);
+//   4. drift on the int32 lattice: xq += rint(v dt 2^30 / R);
+//   5. classification at x_{n+1} on the lattice ("Terminal events").
+// Positions, the mask lookup and the classification are integer or IEEE
+// round-to-nearest FP32 operations without contraction, so they decide the
+// same classes as any other implementation of the same lattice rules.
+#include "kernels.cuh"
+
+namespace mucite {
+
+namespace {
+
+struct Local {
+    float edx, edy, edz, erx, ery, erz, esx, esy, esz;
+    float nsig, T, ux, uy, uz;
+};
+
+// Cell index and fraction along one axis; clamped to the last cell.
+__device__ __forceinline__ void cell_r(float g, int n, int &i0, float &f)
+{
+    int i = __float2int_rd(g);
+    if (i > n - 2) {
+        i0 = n - 2;
+        f = 1.0f;
+    } else {
+        i0 = i;
+        f = g - (float)i;
+    }
+}
+
+__device__ __forceinline__ void cell_z(int32_t zq, int n, int &j0, float &f)
+{
+    const int64_t t = (int64_t)zq * (int64_t)(n - 1);
+    const int64_t j = t >> 30;
+    if (j < 0) {
+        j0 = 0;
+        f = 0.0f;
+    } else if (j > n - 2) {
+        j0 = n - 2;
+        f = 1.0f;
+    } else {
+        j0 = (int)j;
+        f = (float)(t & ((1LL << 30) - 1)) * (1.0f / 1073741824.0f);
+    }
+}
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float4 c, float4 d, float w00, float w10,
+                                        float w01, float w11)
+{
+    return make_float4(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
+                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y,
+                       w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z,
+                       w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w);
+}
+
+__device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float fx, float fy,
+                                       float rr, int32_t zq, Local &L)
+{
+    int i0, j0;
+    float ar, az;
+    cell_r(rr * G.sr, G.nr, i0, ar);
+    cell_z(zq, G.nz, j0, az);
+    const NodeF *nd = G.node + (size_t)j0 * G.nr + i0;
+    const float4 a00 = __ldg(&nd[0].a), a10 = __ldg(&nd[1].a);
+    const float4 a01 = __ldg(&nd[G.nr].a), a11 = __ldg(&nd[G.nr + 1].a);
+    const float4 b00 = __ldg(&nd[0].b), b10 = __ldg(&nd[1].b);
+    const float4 b01 = __ldg(&nd[G.nr].b), b11 = __ldg(&nd[G.nr + 1].b);
+    const float w00 = (1.0f - ar) * (1.0f - az), w10 = ar * (1.0f - az);
+    const float w01 = (1.0f - ar) * az, w11 = ar * az;
+    const float4 fa = lerp4(a00, a10, a01, a11, w00, w10, w01, w11);
+    const float4 fb = lerp4(b00, b10, b01, b11, w00, w10, w01, w11);
+    const float inv = rr > 0.0f ? 1.0f / rr : 0.0f;
+    const float cx = fx * inv, cy = fy * inv; // Eq. 3: zero transverse projection on the axis
+    L.edx = fa.x * cx; L.edy = fa.x * cy; L.edz = fa.y;
+    L.erx = fa.z * cx; L.ery = fa.z * cy; L.erz = fa.w;
+    L.T = fb.y;
+    L.nsig = fb.y > 0.0f ? P.psig * fb.x / fb.y : 0.0f;
+    L.ux = fb.z * cx; L.uy = fb.z * cy; L.uz = fb.w;
+    L.esx = L.esy = L.esz = 0.0f;
+    if (P.esc != nullptr) {
+        int pi0, pj0;
+        float pr, pz;
+        cell_r(rr * P.psr, P.pnr, pi0, pr);
+        cell_z(zq, P.pnz, pj0, pz);
+        const float2 *e = P.esc + (size_t)pj0 * P.pnr + pi0;
+        const float2 e00 = __ldg(&e[0]), e10 = __ldg(&e[1]), e01 = __ldg(&e[P.pnr]),
+                     e11 = __ldg(&e[P.pnr + 1]);
+        const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
+                    v11 = pr * pz;
+        const float er = v00 * e00.x + v10 * e10.x + v01 * e01.x + v11 * e11.x;
+        L.esz = v00 * e00.y + v10 * e10.y + v01 * e01.y + v11 * e11.y;
+        L.esx = er * cx;
+        L.esy = er * cy;
+    }
+}
+
+// T_eff from E_int (kelvin units) through the heat-capacity profile.
+__device__ __forceinline__ float teff_of(const InstF32 &P, float eint)
+{
+    const float e = eint / P.n3;
+    if (e <= P.ecap) return 2.0f * e / (P.c0 + sqrtf(P.c0 * P.c0 + 2.0f * P.c1 * e));
+    return P.tcap + (e - P.ecap);
+}
+
+// Collisions of one pack during one step of length dt. Returns accepted
+// events; sets *ovf when the candidate cap was reached.
+__device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_t pack,
+                                       uint32_t step, float &vx, float &vy, float &vz, float &eint,
+                                       int &ovf)
+{
+    ovf = 0;
+    if (!(L.nsig > 0.0f) || !(L.T > 0.0f)) return 0;
+    const float s = sqrtf(P.s_coef * L.T);
+    const float cbar = 1.1283791670955126f * s; // 2 s / sqrt(pi)
+    float t = 0.0f;
+    int acc = 0;
+    for (int k = 0; k < kKmax; ++k) {
+        const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
+        const float w = sqrtf(wx * wx + wy * wy + wz * wz);
+        const uint4 A = philox10(make_uint4(pack, step, 3u * k, 0u), P.key0, P.key1);
+        t += -__logf(u01f(A.x)) / (L.nsig * (w + cbar));
+        if (t >= P.dt) return acc;
+        const uint4 B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), P.key0, P.key1);
+        float cx, cy, cz, cmag;
+        if (u01f(A.y) * (w + cbar) < w) {
+            // Maxwellian partner, per-component deviation s / sqrt(2)
+            const float sd = 0.70710678118654752f * s;
+            const float r01 = sd * sqrtf(-2.0f * __logf(u01f(B.x)));
+            const float r23 = sd * sqrtf(-2.0f * __logf(u01f(B.z)));
+            float sn, cs, sn2, cs2;
+            sincospif(2.0f * u01f(B.y), &sn, &cs);
+            sincospif(2.0f * u01f(B.w), &sn2, &cs2);
+            cx = r01 * cs;
+            cy = r01 * sn;
+            cz = r23 * cs2;
+            cmag = sqrtf(cx * cx + cy * cy + cz * cz);
+        } else {
+            // speed-weighted Maxwellian: |c|^2 / s^2 ~ Gamma(2, 1), isotropic
+            const float y = -__logf(u01f(B.x)) - __logf(u01f(B.y));
+            cmag = s * sqrtf(y);
+            const float ct = 2.0f * u01f(B.z) - 1.0f;
+            const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+            float sn, cs;
+            sincospif(2.0f * u01f(B.w), &sn, &cs);
+            cx = cmag * st * cs;
+            cy = cmag * st * sn;
+            cz = cmag * ct;
+        }
+        const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        const float g = sqrtf(g2);
+        if (!(u01f(A.z) * (w + cmag) < g)) continue;
+        ++acc;
+        const uint4 Cc = philox10(make_uint4(pack, step, 3u * k + 2u, 0u), P.key0, P.key1);
+        const float Vx = P.fM * vx + P.fm * (L.ux + cx);
+        const float Vy = P.fM * vy + P.fm * (L.uy + cy);
+        const float Vz = P.fM * vz + P.fm * (L.uz + cz);
+        const float etr = P.mu_2kb * g2;
+        const float ec = etr + eint;
+        const float Te = teff_of(P, eint);
+        const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
+        const float omb = -expm1f(__logf(u01f(Cc.z)) / a + __logf(u01f(Cc.w)) / (a + 1.0f));
+        const float etr_new = ec * omb;
+        eint = eint + (etr - etr_new);
+        const float gn = sqrtf(etr_new * P.g_coef) * P.fm;
+        const float ct = 2.0f * u01f(Cc.x) - 1.0f;
+        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        float sn, cs;
+        sincospif(2.0f * u01f(Cc.y), &sn, &cs);
+        vx = Vx + gn * st * cs;
+        vy = Vy + gn * st * sn;
+        vz = Vz + gn * ct;
+    }
+    ovf = 1;
+    return acc;
+}
+
+__device__ __forceinline__ int32_t lattice_step(float d)
+{
+    d = fminf(fmaxf(d, -1.0e9f), 1.0e9f);
+    return __float2int_rn(d);
+}
+
+// Lattice radius in FP32, IEEE round-to-nearest, no contraction.
+__device__ __forceinline__ float lattice_r(float fx, float fy)
+{
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)));
+}
+
+__device__ __forceinline__ int classify(const GridF32 &G, const InstF32 &P, int32_t xq, int32_t yq,
+                                        int32_t zq, float rr)
+{
+    int ir = __float2int_rz(__fadd_rn(__fmul_rn(rr, G.sr), 0.5f));
+    ir = min(ir, G.nr - 1);
+    int64_t iz = ((int64_t)zq * (int64_t)(G.nz - 1) + (1LL << 29)) >> 30;
+    iz = iz < 0 ? 0 : (iz > G.nz - 1 ? G.nz - 1 : iz);
+    const float d = __ldg(&G.dmask[(size_t)iz * G.nr + ir]);
+    if (d <= P.hit) return MUCITE_ELECTRODE;
+    const uint64_t r2 = (uint64_t)((int64_t)xq * xq) + (uint64_t)((int64_t)yq * yq);
+    if (r2 >= (1ULL << 60)) return MUCITE_RADIAL;
+    if (zq >= P.zexit_q) return r2 <= P.rdet2 ? MUCITE_TRANSMITTED : MUCITE_AXIAL;
+    if (zq < 0) return MUCITE_AXIAL;
+    return MUCITE_ACTIVE;
+}
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v)
+{
+    return __reduce_add_sync(0xffffffffu, v);
+}
+
+} // namespace
+
+// grid.x = total tiles over all instances (tile = blockDim.x packs);
+// tile_start[i] = first tile of instance i, tile_start[n_inst] = total.
+__global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 *insts,
+                                                       const int32_t *tile_start, int n_inst,
+                                                       int nsteps)
+{
+    extern __shared__ float s_rf[];
+    __shared__ InstF32 P;
+    __shared__ int64_t s_off;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_start[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        P = insts[lo];
+        s_off = (int64_t)(b - tile_start[lo]) * blockDim.x;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nsteps; k += blockDim.x) {
+        float v = 0.0f;
+        if (P.v_rf != 0.0 && P.dtf != 0.0) {
+            const double x = (double)(P.step0 + k) * P.dtf;
+            v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
+        }
+        s_rf[k] = v;
+    }
+    __syncthreads();
+    const int64_t p = s_off + threadIdx.x;
+    unsigned n_steps_done = 0, n_coll = 0, n_ovf = 0;
+    if (p < P.n_slots && P.status[p] == MUCITE_ACTIVE) {
+        int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
+        float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
+        const uint32_t pack = (uint32_t)p;
+        float fx = (float)xq, fy = (float)yq;
+        float rr = lattice_r(fx, fy);
+        int st = MUCITE_ACTIVE;
+        int k = 0;
+        for (; k < nsteps; ++k) {
+            const uint32_t n = (uint32_t)(P.step0 + k);
+            Local L;
+            gather(G, P, fx, fy, rr, zq, L);
+            int ovf;
+            n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
+            n_ovf += ovf;
+            const float srf = s_rf[k];
+            vx += P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
+            vy += P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
+            vz += P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+            xq += lattice_step(vx * P.cxs);
+            yq += lattice_step(vy * P.cxs);
+            zq += lattice_step(vz * P.czs);
+            fx = (float)xq;
+            fy = (float)yq;
+            rr = lattice_r(fx, fy);
+            st = classify(G, P, xq, yq, zq, rr);
+            if (st != MUCITE_ACTIVE) {
+                ++k;
+                break;
+            }
+        }
+        n_steps_done = (unsigned)k;
+        P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
+        P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
+        P.eint[p] = eint;
+        if (st != MUCITE_ACTIVE) {
+            P.status[p] = (uint8_t)st;
+            P.t_term[p] = (int32_t)(P.step0 + k);
+        }
+    }
+    n_steps_done = warp_sum(n_steps_done);
+    n_coll = warp_sum(n_coll);
+    n_ovf = warp_sum(n_ovf);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_steps_done) atomicAdd(&P.counters[0], (unsigned long long)n_steps_done);
+        if (n_coll) atomicAdd(&P.counters[1], (unsigned long long)n_coll);
+        if (n_ovf) atomicAdd(&P.counters[2], (unsigned long long)n_ovf);
+    }
+}
+
+void launch_step_f32(const GridF32 &G, const InstF32 *d_insts, const int32_t *d_tile_start,
+                     int n_inst, int total_tiles, int threads, int nsteps, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * (size_t)nsteps;
+    step_f32_kernel<<<total_tiles, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, nsteps);
+}
+
+} // namespace mucite

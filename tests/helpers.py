@@ -1,0 +1,76 @@
+"""Shared test plumbing: move identical pack states between the oracle and
+the CUDA library's pools, and ensemble comparisons."""
+import math
+
+import numpy as np
+
+LAT = 2.0 ** 30
+
+
+def lattice_from_fp64(g, x, y, z):
+    """Round FP64 positions to the int32 lattice (rint(x 2^30 / R))."""
+    sx, sz = LAT / g.R, LAT / (g.z1 - g.z0)
+    return (np.rint(np.asarray(x) * sx).astype(np.int32), np.rint(np.asarray(y) * sx).astype(np.int32),
+            np.rint((np.asarray(z) - g.z0) * sz).astype(np.int32))
+
+
+def fp64_from_lattice(g, xq, yq, zq):
+    return (xq.astype(np.float64) * g.R / LAT, yq.astype(np.float64) * g.R / LAT,
+            g.z0 + zq.astype(np.float64) * (g.z1 - g.z0) / LAT)
+
+
+def fp32_state_from_oracle(sim):
+    """Lattice positions + FP32 velocities/E_int of the oracle's packs, and the
+    oracle state reset to exactly the same values (so both start equal)."""
+    n = sim.n
+    g = sim.g
+    xq, yq, zq = lattice_from_fp64(g, sim.x[:n], sim.y[:n], sim.z[:n])
+    st = dict(x=xq, y=yq, z=zq, vx=sim.vx[:n].astype(np.float32), vy=sim.vy[:n].astype(np.float32),
+              vz=sim.vz[:n].astype(np.float32), eint=sim.eint[:n].astype(np.float32),
+              status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy())
+    sim.x[:n], sim.y[:n], sim.z[:n] = fp64_from_lattice(g, xq, yq, zq)
+    sim.vx[:n], sim.vy[:n], sim.vz[:n] = (st[k].astype(np.float64) for k in ("vx", "vy", "vz"))
+    sim.eint[:n] = st["eint"].astype(np.float64)
+    return st
+
+
+def fp64_state_from_oracle(sim):
+    n = sim.n
+    return dict(x=sim.x[:n].copy(), y=sim.y[:n].copy(), z=sim.z[:n].copy(), vx=sim.vx[:n].copy(),
+                vy=sim.vy[:n].copy(), vz=sim.vz[:n].copy(), eint=sim.eint[:n].copy(),
+                status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy())
+
+
+def upload(ctx, inst, arrays, step=0):
+    import torch
+    views = ctx.state(inst)
+    n = len(arrays["status"])
+    for k, a in arrays.items():
+        views[k][:n].copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    torch.cuda.synchronize()
+    ctx.resume(inst, n, step)
+
+
+def download(ctx, inst, n):
+    import torch
+    ctx.sync()
+    torch.cuda.synchronize()
+    return {k: v[:n].cpu().numpy() for k, v in ctx.state(inst).items()}
+
+
+def rel_pos_error(g, got, ref_x, ref_y, ref_z, lattice=True):
+    """Per-pack |x_gpu - x_ref| / |x_ref - (0,0,z0)|."""
+    if lattice:
+        gx, gy, gz = fp64_from_lattice(g, got["x"], got["y"], got["z"])
+    else:
+        gx, gy, gz = got["x"], got["y"], got["z"]
+    d = np.sqrt((gx - ref_x) ** 2 + (gy - ref_y) ** 2 + (gz - ref_z) ** 2)
+    norm = np.sqrt(ref_x ** 2 + ref_y ** 2 + (ref_z - g.z0) ** 2)
+    return d / norm
+
+
+def binomial_band(k_a, k_b, n, nsig=3.0):
+    """|p_a - p_b| within nsig standard deviations of a binomial proportion."""
+    p = 0.5 * (k_a + k_b) / n
+    sd = math.sqrt(max(p * (1 - p), 1.0 / n) / n)
+    return abs(k_a - k_b) / n <= nsig * sd
