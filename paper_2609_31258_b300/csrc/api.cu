@@ -231,6 +231,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.mu_2kb = (float)(mu / (2.0 * kKB));
         P.g_coef = (float)(2.0 * kKB / mu);
         P.n3 = (float)pf.n3;
+        P.inv_n3 = (float)(1.0 / pf.n3);
         P.c0 = (float)pf.c0;
         P.c1 = (float)pf.c1;
         P.tcap = std::isinf(pf.tcap) ? 3.0e38f : (float)pf.tcap;

@@ -97,7 +97,7 @@ struct InstF32 {
     float fM, fm;              // M/(M+m), m/(M+m)
     float mu_2kb;              // mu / (2 k_B): relative KE in kelvin units
     float g_coef;              // 2 k_B / mu
-    float n3, c0, c1, tcap, ecap;
+    float n3, inv_n3, c0, c1, tcap, ecap;
     uint32_t key0, key1;
     int64_t zexit_q;           // first lattice z counted as crossed
     uint64_t rdet2;            // (floor(r_det / R * 2^30))^2

@@ -11,8 +11,15 @@
 //      Borgnakke-Larsen internal exchange;
 //   3. kick v += (q/m)(s_dc E_DC + s_rf(n) E_RF + E_SCE) dt, s_rf from Eq. 4
 //      with the phase taken in FP64 once per (instance, step);
-//   4. drift on the int32 lattice: xq += rint(v dt 2^30 / R);
+//   4. drift on the int32 lattice: xq += floor(v dt 2^30 / R + d), d a
+//      uniform dither;
 //   5. classification at x_{n+1} on the lattice ("Terminal events").
+// Rounding: the per-step lattice displacement and the FP32 velocity update
+// are rounded stochastically (a uniform dither from a hash of pack and step):
+// in ballistic motion the same increment is rounded every step, and
+// round-to-nearest would then add the same error every step; dithered
+// rounding is unbiased and needs no state beyond the pack's own, so results
+// do not depend on how the steps are split into launches.
 // Positions, the mask lookup and the classification are integer or IEEE
 // round-to-nearest FP32 operations without contraction, so they decide the
 // same classes as any other implementation of the same lattice rules.
@@ -21,6 +28,47 @@
 namespace mucite {
 
 namespace {
+
+// MurmurHash3 32-bit finalizer (Appleby): avalanche mix for the dither bits.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Dither in (0,1) from 10 bits of h starting at bit `sh`.
+__device__ __forceinline__ float dither(uint32_t h, int sh)
+{
+    return (float)((h >> sh) & 0x3FFu) * (1.0f / 1024.0f) + (1.0f / 2048.0f);
+}
+
+// v + d with stochastic rounding: the sum is dithered by a uniform offset of
+// one unit in the last place of the result before rounding to nearest.
+__device__ __forceinline__ float add_sr(float v, float d, float u)
+{
+    const float t = v + d;
+    const float ulp = __int_as_float(__float_as_int(t) & 0x7f800000) * 1.1920928955078125e-7f;
+    return v + (d + (u - 0.5f) * ulp);
+}
+
+// sqrt where the value decides nothing discrete (approximate reciprocal root).
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
+// cos and sin of 2 pi u for u in (0,1), through the centred argument
+// 2 pi (u - 1/2) in (-pi, pi) where the hardware approximation is accurate.
+__device__ __forceinline__ void sincos_2pi(float u, float &sn, float &cs)
+{
+    __sincosf(6.283185307179586f * (u - 0.5f), &sn, &cs);
+    sn = -sn;
+    cs = -cs;
+}
 
 struct Local {
     float edx, edy, edz, erx, ery, erz, esx, esy, esz;
@@ -81,12 +129,12 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     const float w01 = (1.0f - ar) * az, w11 = ar * az;
     const float4 fa = lerp4(a00, a10, a01, a11, w00, w10, w01, w11);
     const float4 fb = lerp4(b00, b10, b01, b11, w00, w10, w01, w11);
-    const float inv = rr > 0.0f ? 1.0f / rr : 0.0f;
+    const float inv = rr > 0.0f ? __frcp_rn(rr) : 0.0f;
     const float cx = fx * inv, cy = fy * inv; // Eq. 3: zero transverse projection on the axis
     L.edx = fa.x * cx; L.edy = fa.x * cy; L.edz = fa.y;
     L.erx = fa.z * cx; L.ery = fa.z * cy; L.erz = fa.w;
     L.T = fb.y;
-    L.nsig = fb.y > 0.0f ? P.psig * fb.x / fb.y : 0.0f;
+    L.nsig = fb.y > 0.0f ? __fdividef(P.psig * fb.x, fb.y) : 0.0f;
     L.ux = fb.z * cx; L.uy = fb.z * cy; L.uz = fb.w;
     L.esx = L.esy = L.esz = 0.0f;
     if (P.esc != nullptr) {
@@ -109,8 +157,8 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
 // T_eff from E_int (kelvin units) through the heat-capacity profile.
 __device__ __forceinline__ float teff_of(const InstF32 &P, float eint)
 {
-    const float e = eint / P.n3;
-    if (e <= P.ecap) return 2.0f * e / (P.c0 + sqrtf(P.c0 * P.c0 + 2.0f * P.c1 * e));
+    const float e = eint * P.inv_n3;
+    if (e <= P.ecap) return __fdividef(2.0f * e, P.c0 + sqrt_fast(P.c0 * P.c0 + 2.0f * P.c1 * e));
     return P.tcap + (e - P.ecap);
 }
 
@@ -122,45 +170,45 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
 {
     ovf = 0;
     if (!(L.nsig > 0.0f) || !(L.T > 0.0f)) return 0;
-    const float s = sqrtf(P.s_coef * L.T);
+    const float s = sqrt_fast(P.s_coef * L.T);
     const float cbar = 1.1283791670955126f * s; // 2 s / sqrt(pi)
     float t = 0.0f;
     int acc = 0;
     for (int k = 0; k < kKmax; ++k) {
         const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
-        const float w = sqrtf(wx * wx + wy * wy + wz * wz);
+        const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
         const uint4 A = philox10(make_uint4(pack, step, 3u * k, 0u), P.key0, P.key1);
-        t += -__logf(u01f(A.x)) / (L.nsig * (w + cbar));
+        t += __fdividef(-__logf(u01f(A.x)), L.nsig * (w + cbar));
         if (t >= P.dt) return acc;
         const uint4 B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), P.key0, P.key1);
         float cx, cy, cz, cmag;
         if (u01f(A.y) * (w + cbar) < w) {
             // Maxwellian partner, per-component deviation s / sqrt(2)
             const float sd = 0.70710678118654752f * s;
-            const float r01 = sd * sqrtf(-2.0f * __logf(u01f(B.x)));
-            const float r23 = sd * sqrtf(-2.0f * __logf(u01f(B.z)));
+            const float r01 = sd * sqrt_fast(-2.0f * __logf(u01f(B.x)));
+            const float r23 = sd * sqrt_fast(-2.0f * __logf(u01f(B.z)));
             float sn, cs, sn2, cs2;
-            sincospif(2.0f * u01f(B.y), &sn, &cs);
-            sincospif(2.0f * u01f(B.w), &sn2, &cs2);
+            sincos_2pi(u01f(B.y), sn, cs);
+            sincos_2pi(u01f(B.w), sn2, cs2);
             cx = r01 * cs;
             cy = r01 * sn;
             cz = r23 * cs2;
-            cmag = sqrtf(cx * cx + cy * cy + cz * cz);
+            cmag = sqrt_fast(cx * cx + cy * cy + cz * cz);
         } else {
             // speed-weighted Maxwellian: |c|^2 / s^2 ~ Gamma(2, 1), isotropic
             const float y = -__logf(u01f(B.x)) - __logf(u01f(B.y));
-            cmag = s * sqrtf(y);
+            cmag = s * sqrt_fast(y);
             const float ct = 2.0f * u01f(B.z) - 1.0f;
-            const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+            const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
             float sn, cs;
-            sincospif(2.0f * u01f(B.w), &sn, &cs);
+            sincos_2pi(u01f(B.w), sn, cs);
             cx = cmag * st * cs;
             cy = cmag * st * sn;
             cz = cmag * ct;
         }
         const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
         const float g2 = gx * gx + gy * gy + gz * gz;
-        const float g = sqrtf(g2);
+        const float g = sqrt_fast(g2);
         if (!(u01f(A.z) * (w + cmag) < g)) continue;
         ++acc;
         const uint4 Cc = philox10(make_uint4(pack, step, 3u * k + 2u, 0u), P.key0, P.key1);
@@ -171,14 +219,15 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
         const float ec = etr + eint;
         const float Te = teff_of(P, eint);
         const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
-        const float omb = -expm1f(__logf(u01f(Cc.z)) / a + __logf(u01f(Cc.w)) / (a + 1.0f));
+        // 1 - B for B ~ Beta(a, 2); expm1 keeps the precision of small exchanges
+        const float omb = -expm1f(__fdividef(__logf(u01f(Cc.z)), a) + __fdividef(__logf(u01f(Cc.w)), a + 1.0f));
         const float etr_new = ec * omb;
         eint = eint + (etr - etr_new);
-        const float gn = sqrtf(etr_new * P.g_coef) * P.fm;
+        const float gn = sqrt_fast(etr_new * P.g_coef) * P.fm;
         const float ct = 2.0f * u01f(Cc.x) - 1.0f;
-        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
         float sn, cs;
-        sincospif(2.0f * u01f(Cc.y), &sn, &cs);
+        sincos_2pi(u01f(Cc.y), sn, cs);
         vx = Vx + gn * st * cs;
         vy = Vy + gn * st * sn;
         vz = Vz + gn * ct;
@@ -187,10 +236,12 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
     return acc;
 }
 
-__device__ __forceinline__ int32_t lattice_step(float d)
+// Lattice displacement of one step, floor(d + u) with a uniform dither u,
+// clamped to keep the int32 lattice from wrapping.
+__device__ __forceinline__ int32_t lattice_step(float d, float u)
 {
     d = fminf(fmaxf(d, -1.0e9f), 1.0e9f);
-    return __float2int_rn(d);
+    return __float2int_rd(d + u);
 }
 
 // Lattice radius in FP32, IEEE round-to-nearest, no contraction.
@@ -262,6 +313,7 @@ __global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 
         float rr = lattice_r(fx, fy);
         int st = MUCITE_ACTIVE;
         int k = 0;
+        const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
         for (; k < nsteps; ++k) {
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
@@ -270,12 +322,13 @@ __global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 
             n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
             n_ovf += ovf;
             const float srf = s_rf[k];
-            vx += P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
-            vy += P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
-            vz += P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
-            xq += lattice_step(vx * P.cxs);
-            yq += lattice_step(vy * P.cxs);
-            zq += lattice_step(vz * P.czs);
+            const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
+            vx = add_sr(vx, P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx), dither(h1, 0));
+            vy = add_sr(vy, P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy), dither(h1, 11));
+            vz = add_sr(vz, P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz), dither(h1, 22));
+            xq += lattice_step(vx * P.cxs, dither(h2, 0));
+            yq += lattice_step(vy * P.cxs, dither(h2, 11));
+            zq += lattice_step(vz * P.czs, dither(h2, 22));
             fx = (float)xq;
             fy = (float)yq;
             rr = lattice_r(fx, fy);
