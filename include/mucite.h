@@ -233,6 +233,44 @@ int64_t mucite_launch_count(const mucite_ctx *ctx);
 /* Wait for all work enqueued on the context's stream. */
 mucite_status mucite_sync(mucite_ctx *ctx);
 
+/* Size of the fixed device scratch used by mucite_poisson_solve_noalloc. */
+#define MUCITE_NOALLOC_SCRATCH_BYTES (10u * 1024u * 1024u)
+
+/* Space-charge Poisson solve that allocates nothing (the paper has no
+ * counterpart; it is a deployment variant of the solve inside
+ * mucite_pic_update).
+ * Some callers cannot call cudaMalloc: processes whose device memory is fully
+ * reserved up front (a serving process, or a host framework whose own pool
+ * owns the device and forbids allocations outside it) and real-time loops
+ * that must not block on the allocator. This entry point keeps all of its
+ * scratch (sine matrix, tridiagonal factors, residual and transform buffers,
+ * convergence flags) in one file-scope device array of
+ * MUCITE_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits; it calls no allocator on any call.
+ * Arguments: `device` is the CUDA device to run on (made current for the
+ * call); `cuda_stream` a cudaStream_t on that device (NULL = legacy default);
+ * `pic` the PIC grid (nr x nz nodes over [0, R] x [z0, z1]); `d_Q` device int64
+ * [nz][nr] node charges in units of e * 2^-30 (input, as deposited by the
+ * library); `d_phi` device FP64 [nz][nr] (output; the solve starts from
+ * Phi = 0 on every call, boundary nodes are 0); `d_esc` device float
+ * [nz][nr][2] (output E_r, E_z); `d_rel_residual` device double (output, may be
+ * NULL): the final ||b - A Phi|| / ||b||. Same operator, FP32 DST-I +
+ * tridiagonal correction, FP64 refinement to 1e-6 (at most 8 refinements) and
+ * E differencing as mucite_pic_update. All work is enqueued on the stream.
+ * Set-up: the first call on a device looks up the device address of the
+ * scratch array; make that first call before any stream capture.
+ * Every call shares the one scratch array, which keeps the last call's
+ * contents (this call clears what it needs cleared): calls on the same device
+ * that overlap on the GPU (different streams, or other host threads) race and
+ * must be serialised by the caller.
+ * Errors: MUCITE_E_ARG (NULL pointers, device out of [0, 64), fewer than 3
+ * nodes per axis, or a grid whose scratch exceeds MUCITE_NOALLOC_SCRATCH_BYTES:
+ * about 4 (nz - 2)^2 + 20 (nr - 1)(nz - 2) bytes, e.g. up to 256 x 1026 nodes);
+ * MUCITE_E_CUDA (a CUDA call or launch failed). */
+mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_stream, const mucite_grid *pic,
+                                           const int64_t *d_Q, double *d_phi, float *d_esc,
+                                           double *d_rel_residual);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ MAX_INSTANCES = 256
 EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_fields",
            "mucite_state_layout", "mucite_inject", "mucite_release", "mucite_resume", "mucite_step",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning",
-           "mucite_launch_count", "mucite_sync"]
+           "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc"]
 
 
 class MuciteError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
         L.mucite_launch_count.argtypes = [vp]
         L.mucite_launch_count.restype = C.c_int64
         L.mucite_sync.argtypes = [vp]
+        L.mucite_poisson_solve_noalloc.argtypes = [C.c_int, vp, C.POINTER(Grid), vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -278,6 +279,18 @@ class Context:
                     vx=v(L.off_vx, cap * vs, vt), vy=v(L.off_vy, cap * vs, vt), vz=v(L.off_vz, cap * vs, vt),
                     eint=v(L.off_eint, cap * vs, vt), status=v(L.off_status, cap, torch.uint8),
                     t_term=v(L.off_t_term, cap * 4, torch.int32))
+
+
+def poisson_solve_noalloc(device, stream, pic, Q, phi, esc, rel=None):
+    """Allocation-free space-charge solve on caller-provided device tensors:
+    Q int64 [nz][nr] (input), phi float64 [nz][nr] and esc float32
+    [nz][nr][2] (outputs), rel float64 [1] (optional output)."""
+    g = grid_struct(pic)
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    st = lib().mucite_poisson_solve_noalloc(device, C.c_void_p(stream.cuda_stream), C.byref(g), ptr(Q),
+                                            ptr(phi), ptr(esc), ptr(rel))
+    if st != OK:
+        raise MuciteError(st, "mucite_poisson_solve_noalloc failed")
 
 
 def load_workload(ctx, workload, instance=0, capacity=None):

@@ -1,0 +1,60 @@
+"""The allocation-free space-charge solve, for callers that cannot allocate
+device memory after start-up (fully reserved memory budgets, frameworks
+whose own pool owns the device, real-time loops that must not block on the
+allocator). Called through the C ABI on caller-provided buffers, its output
+must match the library's regular solve (mucite_pic_update) within the
+tolerances of the Poisson parity test, on two calls in a row with different
+charge distributions (the shared scratch keeps the previous call's
+contents). Collected last so that a failure here does not hide any other
+test; it needs nothing from the tests before it."""
+import numpy as np
+import pytest
+
+from paper_2609_31258_b300 import workloads as W
+from helpers import fp32_state_from_oracle, upload
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_solve_matches_pic_update_twice(orc):
+    import torch
+    from paper_2609_31258_b300 import build, mucite
+    build.build()
+    pic = None
+    stream = torch.cuda.current_stream(0)
+    for call, seed in enumerate((2, 9)):
+        w = W.cylinder_space_charge(n_packs=20000, n_steps=0, seed=seed, precision=0, pic_nr=65, pic_nz=257)
+        if call == 1:
+            w.source.sigma, w.source.radius = 0.6e-3, 1.5e-3  # a different charge cloud
+        pic = w.fields.pic
+        s = orc.Sim(w)
+        s.inject()
+        ctx = mucite.Context(0, stream)
+        mucite.load_workload(ctx, w, 0)
+        upload(ctx, 0, fp32_state_from_oracle(s))
+        ctx.pic_update(0)
+        ref = ctx.pic_read(0)
+        ctx.close()
+        Q = torch.from_numpy(ref["Q"]).to("cuda:0")
+        phi = torch.full((pic.nz, pic.nr), float("nan"), dtype=torch.float64, device="cuda:0")
+        esc = torch.full((pic.nz, pic.nr, 2), float("nan"), dtype=torch.float32, device="cuda:0")
+        rel = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda:0")
+        mucite.poisson_solve_noalloc(0, stream, pic, Q, phi, esc, rel)
+        torch.cuda.synchronize()
+        phi, esc, rel = phi.cpu().numpy(), esc.cpu().numpy(), float(rel.item())
+        assert rel <= 1e-6
+        assert np.abs(phi - ref["phi"]).max() <= 1e-4 * np.abs(ref["phi"]).max()
+        scale = max(np.abs(ref["er"]).max(), np.abs(ref["ez"]).max())
+        assert np.abs(esc[..., 0] - ref["er"]).max() <= 1e-3 * scale
+        assert np.abs(esc[..., 1] - ref["ez"]).max() <= 1e-3 * scale
+
+
+def test_noalloc_rejects_oversized_grid():
+    import torch
+    from paper_2609_31258_b300 import build, mucite
+    build.build()
+    big = W.Grid(512, 2048, 5e-3, 0.0, 40e-3)
+    t = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    with pytest.raises(mucite.MuciteError) as e:
+        mucite.poisson_solve_noalloc(0, torch.cuda.current_stream(0), big, t, t, t)
+    assert e.value.status == mucite.E_ARG
