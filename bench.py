@@ -169,6 +169,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-streamed", action="store_true")
+    ap.add_argument("--streamed-packs", type=int, default=8_000_000)
+    ap.add_argument("--serve-requests", type=int, default=8)
+    ap.add_argument("--serve-steps", type=int, default=100_000, help="micro steps per request (50 us)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--section", default="all", choices=["all", "fused", "streamed", "serving"],
+                    help="run only one timed section (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -178,6 +185,17 @@ def main():
     from paper_2609_31258_b300 import build, mucite, workloads as W
 
     ws, rank, local = _dist()
+    if args.section == "serving":
+        torch.cuda.set_device(local)
+        build.build()
+        print(json.dumps(_serving(args, local)))
+        return
+    if args.section == "streamed":
+        torch.cuda.set_device(local)
+        build.build()
+        print(json.dumps(_streamed_push(args, local, torch.cuda.Stream(torch.device("cuda", local)),
+                                        torch.device("cuda", local), _peaks()[0])))
+        return
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -189,7 +207,7 @@ def main():
     w = W.ring_stack(n_packs=args.packs, n_steps=0, seed=1 + rank, precision=0)
     stream = torch.cuda.Stream(dev)
     ctx = mucite.Context(local, stream)
-    ctx.set_tuning(args.spl or 2000, args.threads or 128)
+    ctx.set_tuning(args.spl or 2000, args.threads or 256)
     mucite.load_workload(ctx, w, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -221,15 +239,7 @@ def main():
     T1 = ctx.tally(0)
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     pack_steps = T1["pack_steps"] - T0["pack_steps"]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([pack_steps], device=dev, dtype=torch.float64)
-        dist.all_reduce(p)
-        t_ms, total_ps = float(t.item()), float(p.item())
-    else:
-        total_ps = float(pack_steps)
+    t_ms, total_ps = aggregate(t_ms, pack_steps, dev, ws)
     value = total_ps / (t_ms * 1e-3)
 
     # kernel-level roofline of the fused step kernel: launches of one step
@@ -246,6 +256,10 @@ def main():
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
                 "hbm_bytes_per_pack_step_at_launch": 57.0 / (args.spl or 2000)}
 
+    if args.section == "fused":
+        print(json.dumps({"value": value, "pack_steps_per_step": pack_steps / args.steps,
+                          "launches_per_step": launches_per_step, "ms_per_step": t_ms / args.steps}))
+        return
     # end to end through the C ABI with host buffers: H2D of the pack state
     # from pinned memory, the steps, D2H of the tally
     e2e = _e2e(ctx, args, stream, dev)
@@ -254,6 +268,12 @@ def main():
     fp64 = None
     if not args.no_fp64:
         fp64 = _fp64(args, w, local, stream, dev)
+    streamed = None
+    if not args.no_streamed:
+        streamed = _streamed_push(args, local, stream, dev, peaks)
+    serve = None
+    if not args.no_serving:
+        serve = _serving(args, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -265,17 +285,34 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": w.name, "grid": "512x2048", "packs_per_gpu": args.packs,
                           "micro_steps_per_step": args.micro, "steps_per_launch": args.spl or 2000,
-                          "threads_per_block": args.threads or 128,
+                          "threads_per_block": args.threads or 256,
                           "l2": "flushed before every timed step (256 MiB write)",
                           "parallelism": f"replicas x{ws}"},
                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
                "gpu_launches": int(launches_step), "fp64_plain": fp64,
                "speedup_fp32_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
+               "streamed_push": streamed,
+               "serving": serve,
                "peaks_source": peak_src}
         print(json.dumps(out))
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def aggregate(t_ms, pack_steps, dev, ws):
+    """Whole-job figures over ranks: the slowest rank's time, the sum of the
+    pack-steps every rank advanced (replicas run independently; this is the
+    only collective, outside the timed region)."""
+    if ws <= 1:
+        return float(t_ms), float(pack_steps)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_ms)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(pack_steps)], device=dev, dtype=torch.float64)
+    dist.all_reduce(p)
+    return float(t.item()), float(p.item())
 
 
 def _inst_per_pack_step():
@@ -331,6 +368,68 @@ def _e2e(ctx, args, stream, dev):
     return {"value": per_call * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "note": "pinned host pack state -> device, micro steps, "
                                                      "tally -> host, every step"}
+
+
+def _streamed_push(args, local, stream, dev, peaks):
+    """HBM roofline of the streamed step: one micro step per launch (state
+    read and written every step: 29 + 28 bytes per pack-step) on a
+    collision-free ring-stack workload whose pack pool exceeds L2."""
+    import torch
+    from paper_2609_31258_b300 import mucite, workloads as W
+    n = args.streamed_packs
+    w = W.ring_stack(n_packs=n, n_steps=0, seed=3, precision=0)
+    w.fields.gas_p[:] = 0.0
+    w.source.radius = 2.0e-3
+    ctx = mucite.Context(local, stream)
+    ctx.set_tuning(1, 256)
+    mucite.load_workload(ctx, w, 0)
+    for _ in range(3):
+        ctx.step(0, 1)
+    torch.cuda.synchronize(dev)
+    T0 = ctx.tally(0)
+    K = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ctx.step(0, K)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    T1 = ctx.tally(0)
+    ms = a.elapsed_time(b)
+    ps = T1["pack_steps"] - T0["pack_steps"]
+    layout = mucite.state_layout(mucite.FP32, n)
+    ctx.close()
+    rate = ps / (ms * 1e-3)
+    gbs = 57.0 * rate / 1e9
+    return {"value": rate, "unit": UNIT, "packs": n, "launches": K, "ms": ms,
+            "pool_bytes": int(layout.total_bytes), "bytes_per_pack_step": 57,
+            "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+            "note": "K=1 launches, no gas (push, gather, classify), pool larger than L2"}
+
+
+def _serving(args, local):
+    """Serving loop on the ring-stack geometry: Poisson arrivals at 20 / s,
+    pack counts log-uniform in [1e4, 2e6], three ion templates, 50 us
+    (1e5 micro steps) per request; the first --serve-requests arrivals."""
+    import torch
+    from paper_2609_31258_b300 import mucite, serving, workloads as W
+    base = W.ring_stack(n_packs=1, n_steps=0, precision=0)
+    t, n, tmpl = W.serving_arrivals(n_req=args.serve_requests, rate_hz=20.0, seed=5)
+    reqs = [serving.make_request(i, t[i], int(n[i]), W.SERVING_TEMPLATES[int(tmpl[i])], base,
+                                 n_steps=args.serve_steps, seed=1000 + i) for i in range(args.serve_requests)]
+    ctx = mucite.Context(local)
+    ctx.set_tuning(2000, 256)
+    ctx.load_fields(base.fields)
+    srv = serving.Server(ctx, max_slots=64, chunk=2000)
+    torch.cuda.synchronize()
+    done, wall = srv.run(reqs)
+    ctx.close()
+    lat = serving.latency_summary(done)
+    work = sum(r.tally["pack_steps"] for r in done)
+    return {"requests": len(done), "arrival_rate_hz": 20.0, "micro_steps_per_request": args.serve_steps,
+            "packs": [int(x) for x in n], "templates": [int(x) for x in tmpl],
+            "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"], "mean_latency_s": lat.get("mean_s"),
+            "wall_s": wall, "pack_steps": int(work), "throughput": work / wall, "unit": UNIT,
+            "note": "offered load exceeds capacity at 20 / s: latency is queue dominated"}
 
 
 def _fp64(args, w32, local, stream, dev):

@@ -79,6 +79,12 @@ typedef struct {
     double n_atoms;
     double cv_c0, cv_c1;
     double T_init; /* initial T_eff */
+    /* Transition-state parameters of the dissociation model (Eq. 7,
+     * "Dissociation is modeled as a temperature dependent loss"): activation
+     * enthalpy [kJ/mol] and entropy [J/(mol K)]; dH_kJmol <= 0 disables it.
+     * Every micro step, after the collisions, ln SY -= k(T_eff) dt with the
+     * Eyring rate k = (k_B T/h) exp(dS/R) exp(-dH/(R T)). */
+    double dH_kJmol, dS_JmolK;
 } mucite_ion_template;
 
 /* Source definition ("Continuous current Gaussian source", Eq. 5).
@@ -112,11 +118,12 @@ typedef struct {
 } mucite_run;
 
 /* Byte offsets of the structure-of-arrays pack pool (each array 256-byte
- * aligned). FP32: xq, yq, zq int32; vx, vy, vz, eint float. FP64: x, y, z,
- * vx, vy, vz, eint double. Both: status uint8, t_term int32 (step count at
- * which the pack became terminal, -1 while active). */
+ * aligned). FP32: xq, yq, zq int32; vx, vy, vz, eint, lnsy float. FP64: x, y,
+ * z, vx, vy, vz, eint, lnsy double. Both: status uint8, t_term int32 (step
+ * count at which the pack became terminal, -1 while active). lnsy is the log
+ * of the precursor survival yield of Eq. 7 (0 when dissociation is off). */
 typedef struct {
-    int64_t off_x, off_y, off_z, off_vx, off_vy, off_vz, off_eint, off_status, off_t_term;
+    int64_t off_x, off_y, off_z, off_vx, off_vy, off_vz, off_eint, off_status, off_t_term, off_lnsy;
     int64_t total_bytes;
     int32_t pos_bytes, vel_bytes;
 } mucite_layout;
@@ -127,6 +134,7 @@ typedef struct {
 typedef struct {
     int64_t count[8], weight[8];      /* by status code (index 0..4) */
     double sum_w_ke[8], sum_w_teff[8];/* sum of W * KE [eV] and W * T_eff [K] by status */
+    double sum_w_sy[8];               /* sum of W * SY (surviving precursor weight, Eq. 7) by status */
     int64_t emitted_count, emitted_weight;
     int64_t pack_steps;               /* active pack-steps advanced so far */
     int64_t collisions;               /* accepted collision events so far */
@@ -226,6 +234,18 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
  * `threads_per_block` threads (a multiple of 32, <= 1024). 0 keeps the
  * current value. */
 mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block);
+
+/* Launch mode of the batched FP32 step (the paper runs independent cases as
+ * separate processes, Supporting Information S6; here many instances share
+ * one launch). persistent_blocks_per_sm > 0: a persistent launch of that many
+ * blocks per SM (capped by occupancy) whose blocks take tiles of every
+ * instance from a device work counter; 0: one block per tile.
+ * use_graphs != 0: when all stepped instances share the space-charge
+ * schedule and the context stream is not the legacy default stream, one macro
+ * step (PIC update, RF table, fused step, clock advance) is captured once as
+ * a CUDA graph and replayed.
+ * Errors: MUCITE_E_ARG (persistent_blocks_per_sm outside [0, 32]). */
+mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_sm, int use_graphs);
 
 /* Number of kernels this context has launched since creation. */
 int64_t mucite_launch_count(const mucite_ctx *ctx);

@@ -71,7 +71,7 @@ class OrcFields(C.Structure):
 class OrcIon(C.Structure):
     _fields_ = [("mass_da", C.c_double), ("charge", C.c_double), ("ccs_m2", C.c_double),
                 ("n_atoms", C.c_double), ("cv_c0", C.c_double), ("cv_c1", C.c_double),
-                ("T_init", C.c_double)]
+                ("T_init", C.c_double), ("dH_kJmol", C.c_double), ("dS_JmolK", C.c_double)]
 
 
 class OrcSource(C.Structure):
@@ -90,12 +90,12 @@ class OrcRun(C.Structure):
 class OrcState(C.Structure):
     _fields_ = [("x", _dp), ("y", _dp), ("z", _dp), ("vx", _dp), ("vy", _dp), ("vz", _dp),
                 ("eint", _dp), ("status", _u8p), ("t_term", _i32p), ("ncoll", _i64p),
-                ("nsteps", _i64p), ("noverflow", _i64p)]
+                ("nsteps", _i64p), ("noverflow", _i64p), ("lnsy", _dp)]
 
 
 class OrcTally(C.Structure):
     _fields_ = [("count", C.c_int64 * 8), ("weight", C.c_int64 * 8), ("sum_w_ke", C.c_double * 8),
-                ("sum_w_teff", C.c_double * 8), ("exit_hist", _i64p), ("r_hist", _i64p),
+                ("sum_w_teff", C.c_double * 8), ("sum_w_sy", C.c_double * 8), ("exit_hist", _i64p), ("r_hist", _i64p),
                 ("ke_hist", _i64p), ("teff_hist", _i64p), ("loss_map", _i64p)]
 
 
@@ -115,6 +115,8 @@ def _declare(L):
     L.orc_T_of_eint.restype = C.c_double
     L.orc_cv_of_T.argtypes = [P(OrcIon), C.c_double]
     L.orc_cv_of_T.restype = C.c_double
+    L.orc_eyring_rate.argtypes = [P(OrcIon), C.c_double]
+    L.orc_eyring_rate.restype = C.c_double
     L.orc_efield_from_phi.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
     L.orc_rf_scalar.argtypes = [P(OrcRun), C.c_int64]
     L.orc_rf_scalar.restype = C.c_double
@@ -133,7 +135,7 @@ def _declare(L):
     L.orc_deposit_fixed.argtypes = [C.c_int, C.c_int, C.c_int64, _i32p, _i32p, _i32p, _u8p,
                                     C.c_int64, _i64p]
     L.orc_tally_state.argtypes = [P(OrcFields), P(OrcIon), P(OrcRun), P(OrcTallySpec), C.c_int64,
-                                  _i32p, _i32p, _i32p, _dp, _dp, _dp, _dp, _u8p, _i32p, C.c_int64,
+                                  _i32p, _i32p, _i32p, _dp, _dp, _dp, _dp, _dp, _u8p, _i32p, C.c_int64,
                                   P(OrcTally)]
 
 
@@ -170,7 +172,7 @@ def efield_from_phi(phi, dr, dz):
 
 def ion_struct(ion):
     return OrcIon(ion.mass_da, float(ion.charge), ion.ccs_m2, float(ion.n_atoms), ion.cv_c0,
-                  ion.cv_c1, ion.T_init)
+                  ion.cv_c1, ion.T_init, ion.dH_kJmol, ion.dS_JmolK)
 
 
 def run_struct(run):
@@ -201,6 +203,11 @@ def T_of_eint(ion, e):
 def cv_of_T(ion, T):
     s = ion_struct(ion)
     return lib().orc_cv_of_T(C.byref(s), T)
+
+
+def eyring_rate(ion, T):
+    s = ion_struct(ion)
+    return lib().orc_eyring_rate(C.byref(s), T)
 
 
 def rf_scalar(run, n):
@@ -279,6 +286,7 @@ class Sim:
         self.ncoll = np.zeros(cap, np.int64)
         self.nsteps = np.zeros(cap, np.int64)
         self.noverflow = np.zeros(cap, np.int64)
+        self.lnsy = np.zeros(cap)
         self.n = 0
         self.step = 0
         self.src_acc = 0.0
@@ -299,7 +307,7 @@ class Sim:
         return OrcState(*(_ptr(a, _dp) for a in (self.x, self.y, self.z, self.vx, self.vy, self.vz,
                                                   self.eint)),
                         _ptr(self.status, _u8p), _ptr(self.t_term, _i32p), _ptr(self.ncoll, _i64p),
-                        _ptr(self.nsteps, _i64p), _ptr(self.noverflow, _i64p))
+                        _ptr(self.nsteps, _i64p), _ptr(self.noverflow, _i64p), _ptr(self.lnsy, _dp))
 
     def inject(self, count=None):
         count = self.w.source.n_initial if count is None else count
@@ -370,14 +378,14 @@ class Sim:
             done += chunk
 
     def tally(self, xq=None, yq=None, zq=None, vx=None, vy=None, vz=None, eint=None, status=None,
-              t_term=None):
+              t_term=None, lnsy=None):
         n = self.n
         if xq is None:
             xq, yq, zq = self.quantized()
             vx, vy, vz, eint = self.vx[:n], self.vy[:n], self.vz[:n], self.eint[:n]
-            status, t_term = self.status[:n], self.t_term[:n]
+            status, t_term, lnsy = self.status[:n], self.t_term[:n], self.lnsy[:n]
         return tally_state(self.fields_struct(), self.ion, self.run, xq, yq, zq, vx, vy, vz, eint,
-                           status, t_term, self.w.source.weight)
+                           status, t_term, self.w.source.weight, lnsy)
 
 
 def classify_fixed(fields_struct, run, xq, yq, zq):
@@ -397,12 +405,13 @@ def deposit_fixed(pic, xq, yq, zq, status, qw):
     return Q
 
 
-def tally_state(fields_struct, ion, run, xq, yq, zq, vx, vy, vz, eint, status, t_term, weight):
+def tally_state(fields_struct, ion, run, xq, yq, zq, vx, vy, vz, eint, status, t_term, weight, lnsy=None):
     n = len(status)
     arr = lambda a, t: np.ascontiguousarray(a, t)
     xq, yq, zq = arr(xq, np.int32), arr(yq, np.int32), arr(zq, np.int32)
     vx, vy, vz, eint = (arr(a, np.float64) for a in (vx, vy, vz, eint))
     status, t_term = arr(status, np.uint8), arr(t_term, np.int32)
+    lnsy = arr(lnsy, np.float64) if lnsy is not None else None
     out = dict(exit_hist=np.zeros(run.n_exit_bins, np.int64), r_hist=np.zeros(run.n_r_bins, np.int64),
                ke_hist=np.zeros(run.n_ke_bins, np.int64), teff_hist=np.zeros(run.n_teff_bins, np.int64),
                loss_map=np.zeros((run.n_loss_z, run.n_loss_r), np.int64))
@@ -415,10 +424,11 @@ def tally_state(fields_struct, ion, run, xq, yq, zq, vx, vy, vz, eint, status, t
     spec = tally_spec(run)
     lib().orc_tally_state(C.byref(fields_struct), C.byref(ion_struct(ion)), C.byref(run_struct(run)),
                           C.byref(spec), n, _ptr(xq, _i32p), _ptr(yq, _i32p), _ptr(zq, _i32p),
-                          _ptr(vx, _dp), _ptr(vy, _dp), _ptr(vz, _dp), _ptr(eint, _dp),
+                          _ptr(vx, _dp), _ptr(vy, _dp), _ptr(vz, _dp), _ptr(eint, _dp), _ptr(lnsy, _dp),
                           _ptr(status, _u8p), _ptr(t_term, _i32p), int(weight), C.byref(T))
     out["count"] = np.array(T.count[:], np.int64)
     out["weight"] = np.array(T.weight[:], np.int64)
     out["sum_w_ke"] = np.array(T.sum_w_ke[:])
     out["sum_w_teff"] = np.array(T.sum_w_teff[:])
+    out["sum_w_sy"] = np.array(T.sum_w_sy[:])
     return out

@@ -45,6 +45,8 @@
 #define ORC_DALTON 1.66053906660e-27
 #define ORC_PI 3.14159265358979323846
 #define ORC_KMAX 32 /* candidate collisions examined per pack per step */
+#define ORC_PLANCK 6.62607015e-34
+#define ORC_NA 6.02214076e23
 
 enum { ORC_ACTIVE = 0, ORC_TRANSMITTED = 1, ORC_ELECTRODE = 2, ORC_RADIAL = 3, ORC_AXIAL = 4,
        ORC_EMPTY = 255 };
@@ -111,6 +113,7 @@ typedef struct {
 
 typedef struct {
     double mass_da, charge, ccs_m2, n_atoms, cv_c0, cv_c1, T_init;
+    double dH_kJmol, dS_JmolK; /* transition-state parameters; dH <= 0 disables Eq. 7 */
 } orc_ion;
 
 typedef struct {
@@ -132,6 +135,7 @@ typedef struct {
     int64_t *ncoll;    /* accepted collisions per pack (diagnostic) */
     int64_t *nsteps;   /* active steps advanced per pack */
     int64_t *noverflow;/* steps where the candidate cap was reached */
+    double *lnsy;      /* ln of the precursor survival yield SY (Eq. 7) */
 } orc_state;
 
 /* ------------------------------------------------------------------------- */
@@ -166,6 +170,16 @@ double orc_cv_of_T(const orc_ion *ion, double T)
 {
     double f = ion->cv_c0 + ion->cv_c1 * T;
     return 3.0 * ion->n_atoms * (f < 1.0 ? f : 1.0);
+}
+
+/* Transition-state (Eyring) rate of Eq. 7 at temperature T:
+ * k = (k_B T / h) exp(dS/R) exp(-dH/(R T)), R = k_B N_A. Pinned: closed-form
+ * survival exp(-k t) at constant T_eff; Arrhenius slope d ln(k/T)/d(1/T). */
+double orc_eyring_rate(const orc_ion *ion, double T)
+{
+    if (!(ion->dH_kJmol > 0.0) || !(T > 0.0)) return 0.0;
+    double R = ORC_KB * ORC_NA;
+    return ORC_KB * T / ORC_PLANCK * exp(ion->dS_JmolK / R) * exp(-ion->dH_kJmol * 1000.0 / (R * T));
 }
 
 /* ------------------------------------------------------------------------- */
@@ -303,24 +317,23 @@ static int collide(const orc_ion *ion, const orc_run *run, const orc_local *L, u
         if (t >= run->dt) return accepted;
         double b[4], cp[3], cmag;
         draw4(seed, pack, step, 3u * k + 1u, 0u, b);
+        /* Both partner laws are isotropic with |c'|^2/s^2 ~ Gamma(k, 1):
+         * k = 3/2 for the Maxwellian (components of variance s^2/2), k = 2 for
+         * its speed-weighted form. Gamma(2) = Exp(1) + Exp(1); Gamma(3/2) =
+         * Exp(1) + N^2/2 with N = sqrt(-2 ln u) cos(2 pi u'), so
+         * N^2/2 = -ln(u) cos^2(2 pi u'). */
+        double f = 1.0;
         if (a[1] * (w + cbar) < w) {
-            /* Maxwellian partner: three normals of variance kT/m_g = s^2/2 */
-            double r01 = sqrt(-2.0 * log(b[0])), r23 = sqrt(-2.0 * log(b[2]));
-            double sd = s / sqrt(2.0);
-            cp[0] = sd * r01 * cos(2.0 * ORC_PI * b[1]);
-            cp[1] = sd * r01 * sin(2.0 * ORC_PI * b[1]);
-            cp[2] = sd * r23 * cos(2.0 * ORC_PI * b[3]);
-            cmag = sqrt(cp[0] * cp[0] + cp[1] * cp[1] + cp[2] * cp[2]);
-        } else {
-            /* speed-weighted Maxwellian: |c'|^2/s^2 ~ Gamma(2,1), isotropic */
-            double y = -log(b[0]) - log(b[1]);
-            cmag = s * sqrt(y);
-            double ct = 2.0 * b[2] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-            double ph = 2.0 * ORC_PI * b[3];
-            cp[0] = cmag * st * cos(ph);
-            cp[1] = cmag * st * sin(ph);
-            cp[2] = cmag * ct;
+            double cw = cos(2.0 * ORC_PI * a[3]);
+            f = cw * cw;
         }
+        double y = -log(b[0]) - log(b[1]) * f;
+        cmag = s * sqrt(y);
+        double pct = 2.0 * b[2] - 1.0, pst = sqrt(fmax(0.0, 1.0 - pct * pct));
+        double pph = 2.0 * ORC_PI * b[3];
+        cp[0] = cmag * pst * cos(pph);
+        cp[1] = cmag * pst * sin(pph);
+        cp[2] = cmag * pct;
         double g3[3] = {w3[0] - cp[0], w3[1] - cp[1], w3[2] - cp[2]};
         double g = sqrt(g3[0] * g3[0] + g3[1] * g3[1] + g3[2] * g3[2]);
         if (!(a[2] * (w + cmag) < g)) continue;
@@ -437,6 +450,7 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
         double x = S->x[p], y = S->y[p], z = S->z[p];
         double v[3] = {S->vx[p], S->vy[p], S->vz[p]};
         double eint = S->eint[p];
+        double lnsy = S->lnsy ? S->lnsy[p] : 0.0;
         for (int64_t k = 0; k < nsteps; ++k) {
             int64_t n = step0 + k;
             orc_local L;
@@ -447,6 +461,8 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
             if (S->ncoll) S->ncoll[p] += nc;
             if (S->noverflow) S->noverflow[p] += ovf;
             if (S->nsteps) S->nsteps[p] += 1;
+            /* Eq. 7: the survival yield decays at the rate of the current T_eff */
+            if (ion->dH_kJmol > 0.0) lnsy -= orc_eyring_rate(ion, orc_T_of_eint(ion, eint)) * run->dt;
             for (int d = 0; d < 3; ++d)
                 v[d] += qm * (run->dc_scale * L.Edc[d] + srf[k] * L.Erf[d] + L.Esc[d]) * run->dt;
             x += v[0] * run->dt;
@@ -464,6 +480,7 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
         S->x[p] = x; S->y[p] = y; S->z[p] = z;
         S->vx[p] = v[0]; S->vy[p] = v[1]; S->vz[p] = v[2];
         S->eint[p] = eint;
+        if (S->lnsy) S->lnsy[p] = lnsy;
     }
     free(srf);
 }
@@ -534,6 +551,7 @@ void orc_inject(const orc_ion *ion, const orc_source *src, const orc_run *run, o
         S->eint[p] = e0;
         S->status[p] = ORC_ACTIVE;
         S->t_term[p] = -1;
+        if (S->lnsy) S->lnsy[p] = 0.0;
     }
 }
 
@@ -601,7 +619,7 @@ void orc_deposit_fixed(int pnr, int pnz, int64_t n, const int32_t *xq, const int
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int64_t count[8], weight[8];
-    double sum_w_ke[8], sum_w_teff[8];
+    double sum_w_ke[8], sum_w_teff[8], sum_w_sy[8];
     int64_t *exit_hist;  /* [n_exit_bins] weight of transmitted packs by exit step */
     int64_t *r_hist;     /* [n_r_bins] transmitted weight by exit radius (r <= r_det) */
     int64_t *ke_hist;    /* [n_ke_bins] transmitted weight by kinetic energy */
@@ -619,8 +637,8 @@ static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : 
 void orc_tally_state(const orc_fields *F, const orc_ion *ion, const orc_run *run,
                      const orc_tally_spec *ts, int64_t n, const int32_t *xq, const int32_t *yq,
                      const int32_t *zq, const double *vx, const double *vy, const double *vz,
-                     const double *eint, const uint8_t *status, const int32_t *t_term,
-                     int64_t weight, orc_tally *T)
+                     const double *eint, const double *lnsy, const uint8_t *status,
+                     const int32_t *t_term, int64_t weight, orc_tally *T)
 {
     double M = ion->mass_da * ORC_DALTON;
     double c_ke = 0.5 * M / ORC_E_CHARGE;
@@ -640,6 +658,7 @@ void orc_tally_state(const orc_fields *F, const orc_ion *ion, const orc_run *run
         double te = orc_T_of_eint(ion, eint[p]);
         T->sum_w_ke[st] += (double)weight * ke;
         T->sum_w_teff[st] += (double)weight * te;
+        T->sum_w_sy[st] += (double)weight * (lnsy ? exp(lnsy[p]) : 1.0);
         float fx = (float)xq[p], fy = (float)yq[p];
         float rr = sqrtf(fx * fx + fy * fy);
         if (st == ORC_TRANSMITTED) {

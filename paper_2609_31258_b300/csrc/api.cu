@@ -30,7 +30,7 @@ struct Instance {
     unsigned long long *d_counters = nullptr; // [3]
     // tally buffers: [0..7] count, [8..15] wsum, then hist arrays; sums in d_tsum
     unsigned long long *d_tally = nullptr;
-    double *d_tsum = nullptr; // [16]: sum_ke[8], sum_teff[8]
+    double *d_tsum = nullptr; // [24]: sum_ke[8], sum_teff[8], sum_sy[8]
     int64_t tally_len = 0;
     bool has_pic = false;
     PicInst pic{};
@@ -58,9 +58,21 @@ struct mucite_ctx {
     InstF32 *d_insts = nullptr;
     int32_t *d_tiles = nullptr;
     PicInst *d_picinst = nullptr;
+    DepositArgs *d_dep = nullptr;
+    int32_t *d_dep_tiles = nullptr;
+    float *d_rf = nullptr;       // per-instance RF scalars of the current launch
+    size_t rf_cap = 0;
+    int sm_count = 0;
+    bool gas_free = false;       // no gas anywhere on the static grid
     int steps_per_launch = 256;
     int threads = 256;
+    int persistent = 0;          // blocks per SM of a persistent launch, 0 = one block per tile
+    int use_graphs = 1;
     int64_t launches = 0;
+    // captured macro step of the last group (replayed while the group is unchanged)
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void *> graph_key;
+    int64_t graph_launches = 0;
 };
 
 namespace {
@@ -131,6 +143,7 @@ void layout_of(int precision, int64_t cap, mucite_layout *L)
     put(L->off_eint, cap * vb);
     put(L->off_status, cap);
     put(L->off_t_term, cap * 4);
+    put(L->off_lnsy, cap * vb);
     L->total_bytes = off;
     L->pos_bytes = pb;
     L->vel_bytes = vb;
@@ -216,6 +229,10 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.eint = at<float>(I.pool, I.lay.off_eint);
         P.status = at<uint8_t>(I.pool, I.lay.off_status);
         P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+        P.lnsy = at<float>(I.pool, I.lay.off_lnsy);
+        P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
+        P.tst_a_dt = (float)(kKB / kPlanck * exp(ion.dS_JmolK / kR) * r.dt);
+        P.tst_b = (float)(ion.dH_kJmol * 1000.0 / kR);
         P.v_rf = r.v_rf;
         P.dtf = r.dt * r.f_rf;
         P.phi_rf = r.phi_rf;
@@ -260,6 +277,10 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.eint = at<double>(I.pool, I.lay.off_eint);
         P.status = at<uint8_t>(I.pool, I.lay.off_status);
         P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
+        P.lnsy = at<double>(I.pool, I.lay.off_lnsy);
+        P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
+        P.tst_a = kKB / kPlanck * exp(ion.dS_JmolK / kR);
+        P.tst_b = ion.dH_kJmol * 1000.0 / kR;
         P.qm = ion.charge * kE / (ion.mass_da * kDa);
         P.dc_scale = r.dc_scale;
         P.dt = r.dt;
@@ -347,6 +368,7 @@ mucite_status inject_packs(mucite_ctx *ctx, Instance &I, int64_t p0, int64_t cou
     A.vy = (char *)I.pool + I.lay.off_vy;
     A.vz = (char *)I.pool + I.lay.off_vz;
     A.eint = (char *)I.pool + I.lay.off_eint;
+    A.lnsy = (char *)I.pool + I.lay.off_lnsy;
     A.status = at<uint8_t>(I.pool, I.lay.off_status);
     A.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
     A.R = ctx->g.R;
@@ -376,11 +398,8 @@ int64_t source_emit(Instance &I, int64_t nsteps)
     return emitted;
 }
 
-mucite_status pic_update_one(mucite_ctx *ctx, Instance &I)
+DepositArgs deposit_args(const mucite_ctx *ctx, const Instance &I)
 {
-    const PicGeom &G = ctx->pg;
-    const size_t nn = (size_t)G.pnr * G.pnz;
-    CK(cudaMemsetAsync(I.pic.Q, 0, nn * sizeof(unsigned long long), ctx->stream));
     DepositArgs D{};
     D.precision = I.run.precision;
     D.x = (char *)I.pool + I.lay.off_x;
@@ -391,17 +410,52 @@ mucite_status pic_update_one(mucite_ctx *ctx, Instance &I)
     D.sx = kLat / ctx->g.R;
     D.sz = kLat / (ctx->g.z1 - ctx->g.z0);
     D.gz0 = ctx->g.z0;
-    D.pnr = G.pnr;
-    D.pnz = G.pnz;
+    D.pnr = ctx->pg.pnr;
+    D.pnz = ctx->pg.pnz;
     D.qw = (int64_t)I.ion.charge * I.src.weight;
     D.Q = I.pic.Q;
-    launch_deposit(D, ctx->stream);
-    ctx->launches++;
-    CKL();
-    CK(cudaMemsetAsync(I.pic.red, 0, 4 * sizeof(double), ctx->stream));
-    CK(cudaMemsetAsync(I.pic.conv, 0, sizeof(int), ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d_picinst, &I.pic, sizeof(PicInst), cudaMemcpyHostToDevice, ctx->stream));
-    ctx->launches += launch_pic_solve(G, ctx->d_picinst, 1, 8, 1e-6, ctx->stream);
+    return D;
+}
+
+// Upload the descriptors of a space-charge group (outside any capture).
+mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, int &total_tiles)
+{
+    const size_t n = grp.size();
+    std::vector<DepositArgs> dep(n);
+    std::vector<PicInst> pi(n);
+    std::vector<int32_t> tiles(n + 1);
+    int64_t total = 0;
+    for (size_t k = 0; k < n; ++k) {
+        dep[k] = deposit_args(ctx, *grp[k]);
+        pi[k] = grp[k]->pic;
+        tiles[k] = (int32_t)total;
+        total += (grp[k]->n_slots + 255) / 256;
+    }
+    tiles[n] = (int32_t)total;
+    total_tiles = (int)total;
+    CK(cudaMemcpyAsync(ctx->d_dep, dep.data(), n * sizeof(DepositArgs), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_dep_tiles, tiles.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_picinst, pi.data(), n * sizeof(PicInst), cudaMemcpyHostToDevice, ctx->stream));
+    return MUCITE_OK;
+}
+
+// Space-charge macro step of a group: clear, deposit, solve, E_SCE -- a fixed
+// number of launches for any number of instances.
+int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles)
+{
+    launch_pic_prepare(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
+    launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
+    return 2 + launch_pic_solve(ctx->pg, ctx->d_picinst, n_inst, 8, 1e-6, ctx->stream);
+}
+
+mucite_status pic_update_group(mucite_ctx *ctx, const std::vector<Instance *> &grp)
+{
+    if (grp.empty()) return MUCITE_OK;
+    int total = 0;
+    const mucite_status st = pic_upload(ctx, grp, total);
+    if (st != MUCITE_OK) return st;
+    ctx->launches += pic_launch(ctx, (int)grp.size(), total);
     CKL();
     return MUCITE_OK;
 }
@@ -415,44 +469,157 @@ mucite_status check_instance(mucite_ctx *ctx, int instance)
     return MUCITE_OK;
 }
 
-// Advance a group of FP32 instances together by nsteps (one launch per chunk).
+void drop_graph(mucite_ctx *ctx)
+{
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->graph_key.clear();
+}
+
+mucite_status ensure_rf(mucite_ctx *ctx, size_t floats)
+{
+    if (floats <= ctx->rf_cap) return MUCITE_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    dfree(ctx->d_rf);
+    CK(cudaMalloc(&ctx->d_rf, floats * sizeof(float)));
+    ctx->rf_cap = floats;
+    return MUCITE_OK;
+}
+
+// Upload the step descriptors of a group (clocks, slot counts, tiles).
+mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, int chunk, int &total_tiles)
+{
+    const size_t n = grp.size();
+    std::vector<InstF32> host(n);
+    std::vector<int32_t> tiles(n + 1);
+    int64_t total = 0;
+    for (size_t k = 0; k < n; ++k) {
+        Instance *I = grp[k];
+        host[k] = I->f32;
+        host[k].n_slots = I->n_slots;
+        host[k].step0 = I->step;
+        host[k].rf = ctx->d_rf + k * (size_t)chunk;
+        tiles[k] = (int32_t)total;
+        total += (I->n_slots + ctx->threads - 1) / ctx->threads;
+    }
+    tiles[n] = (int32_t)total;
+    if (total > INT32_MAX) return fail(ctx, MUCITE_E_ARG, "too many tiles in one launch");
+    total_tiles = (int)total;
+    CK(cudaMemcpyAsync(ctx->d_insts, host.data(), sizeof(InstF32) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return MUCITE_OK;
+}
+
+// Collisions can happen only with gas on the grid, a non-zero pressure scale
+// and a non-zero cross section (otherwise the collision-free kernel runs).
+bool can_collide(const mucite_ctx *ctx, const Instance &I)
+{
+    return !ctx->gas_free && I.run.p_scale > 0.0 && I.ion.ccs_m2 > 0.0;
+}
+
+int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int total_tiles, int chunk)
+{
+    if (total_tiles <= 0) return 0;
+    bool collide = false;
+    for (const Instance *I : grp) collide = collide || can_collide(ctx, *I);
+    int grid = total_tiles;
+    if (ctx->persistent > 0) {
+        const int per_sm =
+            std::min(ctx->persistent, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide)));
+        grid = std::min(total_tiles, per_sm * ctx->sm_count);
+    }
+    launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,
+                    chunk, grid, collide, ctx->stream);
+    return 2;
+}
+
+// Advance a group of FP32 instances together by nsteps: per chunk, the
+// space-charge macro step of the instances that are due, then one fused
+// launch over the packs of all instances. When every instance shares the
+// PIC schedule, a whole macro step is captured once as a CUDA graph (PIC,
+// RF table, step, clock advance on the device) and replayed.
 mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int64_t nsteps)
 {
-    std::vector<InstF32> host(grp.size());
-    std::vector<int32_t> tiles(grp.size() + 1);
+    const size_t n = grp.size();
+    const int P0 = grp[0]->has_pic ? grp[0]->run.pic_interval : 0;
+    bool uniform = true;
+    for (Instance *I : grp) {
+        const int P = I->has_pic ? I->run.pic_interval : 0;
+        uniform = uniform && P == P0 && (P == 0 || I->step % P == 0);
+    }
     int64_t done = 0;
+    // the legacy default stream cannot be captured
+    const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy;
+    if (ctx->use_graphs && uniform && capturable) {
+        const int chunk = P0 > 0 ? P0 : ctx->steps_per_launch;
+        const int64_t reps = (nsteps - done) / chunk;
+        if (reps >= 2) {
+            mucite_status st = ensure_rf(ctx, n * (size_t)chunk);
+            if (st != MUCITE_OK) return st;
+            std::vector<const void *> key;
+            key.push_back((const void *)(intptr_t)chunk);
+            key.push_back((const void *)(intptr_t)ctx->threads);
+            key.push_back((const void *)(intptr_t)ctx->persistent);
+            for (Instance *I : grp) {
+                key.push_back(I);
+                key.push_back((const void *)(intptr_t)I->n_slots);
+            }
+            int tiles = 0, ptiles = 0;
+            st = step_upload(ctx, grp, chunk, tiles);
+            if (st != MUCITE_OK) return st;
+            if (P0 > 0) {
+                st = pic_upload(ctx, grp, ptiles);
+                if (st != MUCITE_OK) return st;
+            }
+            if (!ctx->graph || key != ctx->graph_key) {
+                drop_graph(ctx);
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                int64_t l = 0;
+                if (P0 > 0) l += pic_launch(ctx, (int)n, ptiles);
+                l += step_launch(ctx, grp, tiles, chunk);
+                launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
+                l += 1;
+                const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+                if (ce != cudaSuccess) return fail(ctx, MUCITE_E_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+                const cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) {
+                    ctx->graph = nullptr;
+                    return fail(ctx, MUCITE_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+                }
+                ctx->graph_key = key;
+                ctx->graph_launches = l;
+            }
+            for (int64_t r = 0; r < reps; ++r) {
+                CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+                ctx->launches += ctx->graph_launches;
+            }
+            for (Instance *I : grp) I->step += reps * chunk;
+            done += reps * chunk;
+        }
+    }
     while (done < nsteps) {
         int64_t chunk = std::min<int64_t>(nsteps - done, ctx->steps_per_launch);
+        std::vector<Instance *> due;
         for (Instance *I : grp) {
             const int P = I->has_pic ? I->run.pic_interval : 0;
             if (P > 0) {
-                if (I->step % P == 0) {
-                    const mucite_status st = pic_update_one(ctx, *I);
-                    if (st != MUCITE_OK) return st;
-                }
+                if (I->step % P == 0) due.push_back(I);
                 chunk = std::min<int64_t>(chunk, P - I->step % P);
             }
         }
-        int64_t total = 0;
-        for (size_t k = 0; k < grp.size(); ++k) {
-            Instance *I = grp[k];
-            host[k] = I->f32;
-            host[k].n_slots = I->n_slots;
-            host[k].step0 = I->step;
-            tiles[k] = (int32_t)total;
-            total += (I->n_slots + ctx->threads - 1) / ctx->threads;
-        }
-        tiles[grp.size()] = (int32_t)total;
-        if (total > 0) {
-            CK(cudaMemcpyAsync(ctx->d_insts, host.data(), sizeof(InstF32) * grp.size(),
-                               cudaMemcpyHostToDevice, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(int32_t) * (grp.size() + 1),
-                               cudaMemcpyHostToDevice, ctx->stream));
-            launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), (int)total,
-                            ctx->threads, (int)chunk, ctx->stream);
-            ctx->launches++;
-            CKL();
-        }
+        mucite_status st = pic_update_group(ctx, due);
+        if (st != MUCITE_OK) return st;
+        st = ensure_rf(ctx, n * (size_t)chunk);
+        if (st != MUCITE_OK) return st;
+        int tiles = 0;
+        st = step_upload(ctx, grp, (int)chunk, tiles);
+        if (st != MUCITE_OK) return st;
+        ctx->launches += step_launch(ctx, grp, tiles, (int)chunk);
+        CKL();
         for (Instance *I : grp) I->step += chunk;
         done += chunk;
     }
@@ -465,7 +632,8 @@ mucite_status step_f64_one(mucite_ctx *ctx, Instance &I, int64_t nsteps)
     for (int64_t k = 0; k < nsteps; ++k) {
         const int P = I.has_pic ? I.run.pic_interval : 0;
         if (P > 0 && I.step % P == 0) {
-            const mucite_status st = pic_update_one(ctx, I);
+            std::vector<Instance *> one{&I};
+            const mucite_status st = pic_update_group(ctx, one);
             if (st != MUCITE_OK) return st;
         }
         InstF64 p = I.f64;
@@ -497,11 +665,16 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     cudaError_t e = cudaMalloc(&ctx->d_insts, sizeof(InstF32) * MUCITE_MAX_INSTANCES);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_picinst, sizeof(PicInst) * MUCITE_MAX_INSTANCES);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep, sizeof(DepositArgs) * MUCITE_MAX_INSTANCES);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         fail(nullptr, MUCITE_E_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
         dfree(ctx->d_insts);
         dfree(ctx->d_tiles);
         dfree(ctx->d_picinst);
+        dfree(ctx->d_dep);
+        dfree(ctx->d_dep_tiles);
         delete ctx;
         return MUCITE_E_OOM;
     }
@@ -520,6 +693,10 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_insts);
     dfree(ctx->d_tiles);
     dfree(ctx->d_picinst);
+    dfree(ctx->d_dep);
+    dfree(ctx->d_dep_tiles);
+    dfree(ctx->d_rf);
+    drop_graph(ctx);
     delete ctx;
 }
 
@@ -575,6 +752,8 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
     CK(cudaMemcpyAsync(ctx->d_f64[7], gas_uz, nb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(d_dist, surf_dist, nb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(d_mask, metal_mask, n, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->gas_free = true;
+    for (int64_t k = 0; k < n && ctx->gas_free; ++k) ctx->gas_free = !(gas_p[k] > 0.0);
     const double dr = g->R / (g->nr - 1), dz = (g->z1 - g->z0) / (g->nz - 1);
     launch_efield(d_phi, g->nr, g->nz, dr, dz, ctx->d_f64[0], ctx->d_f64[1], ctx->stream);
     launch_efield(d_phi + n, g->nr, g->nz, dr, dz, ctx->d_f64[2], ctx->d_f64[3], ctx->stream);
@@ -695,6 +874,7 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
                         bound);
     }
     DevGuard dg(ctx->device);
+    drop_graph(ctx);
     Instance &I = ctx->inst[instance];
     if (I.used) {
         cudaStreamSynchronize(ctx->stream);
@@ -712,7 +892,7 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
     I.tally_len = 16 + run->n_exit_bins + run->n_r_bins + run->n_ke_bins + run->n_teff_bins +
                   (int64_t)run->n_loss_r * run->n_loss_z;
     CK(cudaMalloc(&I.d_tally, I.tally_len * sizeof(unsigned long long)));
-    CK(cudaMalloc(&I.d_tsum, 16 * sizeof(double)));
+    CK(cudaMalloc(&I.d_tsum, 24 * sizeof(double)));
     I.has_pic = pic_on;
     if (pic_on) {
         const PicGeom &G = ctx->pg;
@@ -752,6 +932,7 @@ mucite_status mucite_release(mucite_ctx *ctx, int instance)
     if (st != MUCITE_OK) return st;
     DevGuard dg(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
     free_instance(ctx->inst[instance]);
     return MUCITE_OK;
 }
@@ -765,6 +946,7 @@ mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int6
         return fail(ctx, MUCITE_E_ARG, "n_slots %lld / step %lld out of range", (long long)n_slots,
                     (long long)step);
     DevGuard dg(ctx->device);
+    drop_graph(ctx);
     I.n_slots = n_slots;
     I.step = step;
     CK(cudaMemsetAsync(I.d_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
@@ -828,7 +1010,8 @@ mucite_status mucite_pic_update(mucite_ctx *ctx, int instance)
     Instance &I = ctx->inst[instance];
     if (!I.has_pic) return fail(ctx, MUCITE_E_STATE, "instance %d has no space charge", instance);
     DevGuard dg(ctx->device);
-    return pic_update_one(ctx, I);
+    std::vector<Instance *> one{&I};
+    return pic_update_group(ctx, one);
 }
 
 mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
@@ -840,7 +1023,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     const mucite_run &r = I.run;
     DevGuard dg(ctx->device);
     CK(cudaMemsetAsync(I.d_tally, 0, I.tally_len * sizeof(unsigned long long), ctx->stream));
-    CK(cudaMemsetAsync(I.d_tsum, 0, 16 * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(I.d_tsum, 0, 24 * sizeof(double), ctx->stream));
     TallyArgs A{};
     A.precision = r.precision;
     A.x = (char *)I.pool + I.lay.off_x;
@@ -850,6 +1033,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     A.vy = (char *)I.pool + I.lay.off_vy;
     A.vz = (char *)I.pool + I.lay.off_vz;
     A.eint = (char *)I.pool + I.lay.off_eint;
+    A.lnsy = (char *)I.pool + I.lay.off_lnsy;
     A.status = at<uint8_t>(I.pool, I.lay.off_status);
     A.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
     A.n = I.n_slots;
@@ -875,6 +1059,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     A.wsum = I.d_tally + 8;
     A.sum_ke = I.d_tsum;
     A.sum_teff = I.d_tsum + 8;
+    A.sum_sy = I.d_tsum + 16;
     A.exit_hist = I.d_tally + 16;
     A.r_hist = A.exit_hist + r.n_exit_bins;
     A.ke_hist = A.r_hist + r.n_r_bins;
@@ -884,7 +1069,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     ctx->launches++;
     CKL();
     std::vector<unsigned long long> h(I.tally_len);
-    double sums[16];
+    double sums[24];
     unsigned long long cnt[3];
     CK(cudaMemcpyAsync(h.data(), I.d_tally, I.tally_len * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, ctx->stream));
@@ -896,6 +1081,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
         out->weight[k] = (int64_t)h[8 + k];
         out->sum_w_ke[k] = sums[k];
         out->sum_w_teff[k] = sums[8 + k];
+        out->sum_w_sy[k] = sums[16 + k];
     }
     out->emitted_count = I.n_slots;
     out->emitted_weight = I.n_slots * I.src.weight;
@@ -951,8 +1137,21 @@ mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threa
         return fail(ctx, MUCITE_E_ARG, "steps_per_launch must be in [1, 12000]");
     if (threads_per_block < 0 || threads_per_block % 32 != 0 || threads_per_block > 256)
         return fail(ctx, MUCITE_E_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
+    drop_graph(ctx);
     if (steps_per_launch) ctx->steps_per_launch = steps_per_launch;
     if (threads_per_block) ctx->threads = threads_per_block;
+    return MUCITE_OK;
+}
+
+mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_sm, int use_graphs)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (persistent_blocks_per_sm < 0 || persistent_blocks_per_sm > 32)
+        return fail(ctx, MUCITE_E_ARG, "persistent_blocks_per_sm must be in [0, 32]");
+    DevGuard dg(ctx->device);
+    drop_graph(ctx);
+    ctx->persistent = persistent_blocks_per_sm;
+    ctx->use_graphs = use_graphs ? 1 : 0;
     return MUCITE_OK;
 }
 

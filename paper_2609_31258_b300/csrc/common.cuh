@@ -15,6 +15,8 @@ constexpr double kKB = 1.380649e-23;       // Boltzmann constant [J/K]
 constexpr double kDa = 1.66053906660e-27;  // dalton [kg]
 constexpr double kEps0 = 8.8541878128e-12; // vacuum permittivity [F/m]
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kPlanck = 6.62607015e-34;           // Planck constant [J s]
+constexpr double kR = 1.380649e-23 * 6.02214076e23;  // molar gas constant k_B N_A [J/(mol K)]
 constexpr double kLat = 1073741824.0;      // 2^30 lattice units per R (r) or per (z1 - z0) (z)
 constexpr int kKmax = 32;                  // collision candidates examined per pack per step
 
@@ -82,12 +84,13 @@ struct Profile {
 // a device array; copied to shared memory by every block).
 struct InstF32 {
     int32_t *xq, *yq, *zq;
-    float *vx, *vy, *vz, *eint;
+    float *vx, *vy, *vz, *eint, *lnsy;
     uint8_t *status;
     int32_t *t_term;
     int64_t n_slots;
     int64_t step0;
     double v_rf, dtf, phi_rf;  // RF scalar V * cos(2 pi frac(n dt f) + phi), FP64
+    float *rf;                 // RF scalars of the current launch, one per micro step
     float kick;                // q e dt / m
     float dc_scale;
     float cxs, czs;            // dt * 2^30 / R, dt * 2^30 / (z1 - z0): velocity -> lattice step
@@ -98,6 +101,8 @@ struct InstF32 {
     float mu_2kb;              // mu / (2 k_B): relative KE in kelvin units
     float g_coef;              // 2 k_B / mu
     float n3, inv_n3, c0, c1, tcap, ecap;
+    int tst;                   // dissociation (Eq. 7) on
+    float tst_a_dt, tst_b;     // k dt = tst_a_dt * T * exp(-tst_b / T)
     uint32_t key0, key1;
     int64_t zexit_q;           // first lattice z counted as crossed
     uint64_t rdet2;            // (floor(r_det / R * 2^30))^2
@@ -110,12 +115,14 @@ struct InstF32 {
 
 // Per-instance parameters of the plain FP64 step.
 struct InstF64 {
-    double *x, *y, *z, *vx, *vy, *vz, *eint;
+    double *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy;
     uint8_t *status;
     int32_t *t_term;
     int64_t n_slots;
     double qm, dc_scale, dt, p_scale, sigma, M, mg, T_unused;
     Profile prof;
+    int tst;
+    double tst_a, tst_b;       // k = tst_a * T * exp(-tst_b / T)
     uint64_t seed;
     int64_t zexit_q, rdet_q;
     float hit;

@@ -50,6 +50,7 @@ __global__ void inject_kernel(InjectArgs A)
         ((float *)A.vy)[p] = (float)vy;
         ((float *)A.vz)[p] = (float)vz;
         ((float *)A.eint)[p] = (float)A.e0;
+        ((float *)A.lnsy)[p] = 0.0f;
     } else {
         ((double *)A.x)[p] = x;
         ((double *)A.y)[p] = y;
@@ -58,6 +59,7 @@ __global__ void inject_kernel(InjectArgs A)
         ((double *)A.vy)[p] = vy;
         ((double *)A.vz)[p] = vz;
         ((double *)A.eint)[p] = A.e0;
+        ((double *)A.lnsy)[p] = 0.0;
     }
     A.status[p] = MUCITE_ACTIVE;
     A.t_term[p] = -1;

@@ -11,7 +11,7 @@ struct InjectArgs {
     double z_plane, radius, sigma, sd, pz0, pz1, e0;
     uint32_t key0, key1;
     int precision;
-    void *x, *y, *z, *vx, *vy, *vz, *eint;
+    void *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy;
     uint8_t *status;
     int32_t *t_term;
     double R, gz0, gz1;
@@ -19,7 +19,7 @@ struct InjectArgs {
 
 struct TallyArgs {
     int precision;
-    const void *x, *y, *z, *vx, *vy, *vz, *eint;
+    const void *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy;
     const uint8_t *status;
     const int32_t *t_term;
     int64_t n;
@@ -30,14 +30,17 @@ struct TallyArgs {
     int exit_bin_steps, n_exit_bins, n_r_bins, n_ke_bins, n_teff_bins, n_loss_r, n_loss_z;
     int64_t weight;
     unsigned long long *count, *wsum;  // [8]
-    double *sum_ke, *sum_teff;         // [8]
+    double *sum_ke, *sum_teff, *sum_sy; // [8] each
     unsigned long long *exit_hist, *r_hist, *ke_hist, *teff_hist, *loss_map;
 };
 
 void launch_inject(const InjectArgs &A, cudaStream_t s);
 void launch_tally(const TallyArgs &A, cudaStream_t s);
-void launch_step_f32(const GridF32 &G, const InstF32 *d_insts, const int32_t *d_tile_start,
-                     int n_inst, int total_tiles, int threads, int nsteps, cudaStream_t s);
+// grid == total_tiles: one tile per block; a smaller grid strides over the tiles.
+void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
+                     int total_tiles, int threads, int nsteps, int grid, bool collide, cudaStream_t s);
+void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
+int step_f32_blocks_per_sm(int threads, int nsteps, bool collide);
 void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, cudaStream_t s);
 
 } // namespace mucite

@@ -61,9 +61,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 } // namespace
 
-__global__ void __launch_bounds__(256) deposit_kernel(DepositArgs A)
+__device__ __forceinline__ void deposit_one(const DepositArgs &A, int64_t p)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= A.n || A.status[p] != MUCITE_ACTIVE) return;
     int32_t xq, yq, zq;
     if (A.precision == MUCITE_FP32) {
@@ -91,6 +90,39 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepositArgs A)
     atomicAdd(Q + 1, (unsigned long long)(A.qw * wr1 * wz0));
     atomicAdd(Q + A.pnr, (unsigned long long)(A.qw * wr0 * wz1));
     atomicAdd(Q + A.pnr + 1, (unsigned long long)(A.qw * wr1 * wz1));
+}
+
+// Tile t of 256 packs belongs to instance i with tile_start[i] <= t < tile_start[i+1].
+__global__ void __launch_bounds__(256) deposit_kernel(const DepositArgs *args, const int32_t *tile_start,
+                                                      int n_inst)
+{
+    __shared__ int s_inst;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_start[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        s_inst = lo;
+    }
+    __syncthreads();
+    const int inst = s_inst;
+    deposit_one(args[inst], (int64_t)(b - tile_start[inst]) * blockDim.x + threadIdx.x);
+}
+
+// Clears the node charges and the convergence bookkeeping of every instance
+// before a macro step (blockIdx.y = instance).
+__global__ void __launch_bounds__(256) pic_prepare_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.y];
+    const int64_t n = (int64_t)G.pnr * G.pnz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        I.Q[e] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x < 4) I.red[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
 }
 
 // ||b||^2 over the unknowns; also clears the convergence flag and counters.
@@ -266,10 +298,18 @@ __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *inst
     }
 }
 
-void launch_deposit(const DepositArgs &A, cudaStream_t s)
+void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
-    if (A.n <= 0) return;
-    deposit_kernel<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+    const int64_t nn = (int64_t)G.pnr * G.pnz;
+    const unsigned bx = (unsigned)std::min<int64_t>((nn + 255) / 256, 512);
+    pic_prepare_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(G, d_insts);
+}
+
+void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,
+                    cudaStream_t s)
+{
+    if (total_tiles <= 0) return;
+    deposit_kernel<<<total_tiles, 256, 0, s>>>(d_args, d_tile_start, n_inst);
 }
 
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,

@@ -51,7 +51,11 @@ struct DstGemm {
     float alpha;
 };
 
-void launch_deposit(const DepositArgs &A, cudaStream_t s);
+// Batched over instances: tile t of 256 packs belongs to the instance i with
+// tile_start[i] <= t < tile_start[i + 1].
+void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,
+                    cudaStream_t s);
+void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 // Returns the number of kernel launches issued.
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
                      cudaStream_t s);

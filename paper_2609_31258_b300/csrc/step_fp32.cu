@@ -181,23 +181,19 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
         t += __fdividef(-__logf(u01f(A.x)), L.nsig * (w + cbar));
         if (t >= P.dt) return acc;
         const uint4 B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), P.key0, P.key1);
-        float cx, cy, cz, cmag;
+        // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
+        // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
+        // N^2/2 = -ln(u) cos^2(2 pi u'). One branch-free path for both laws.
+        float f = 1.0f;
         if (u01f(A.y) * (w + cbar) < w) {
-            // Maxwellian partner, per-component deviation s / sqrt(2)
-            const float sd = 0.70710678118654752f * s;
-            const float r01 = sd * sqrt_fast(-2.0f * __logf(u01f(B.x)));
-            const float r23 = sd * sqrt_fast(-2.0f * __logf(u01f(B.z)));
-            float sn, cs, sn2, cs2;
-            sincos_2pi(u01f(B.y), sn, cs);
-            sincos_2pi(u01f(B.w), sn2, cs2);
-            cx = r01 * cs;
-            cy = r01 * sn;
-            cz = r23 * cs2;
-            cmag = sqrt_fast(cx * cx + cy * cy + cz * cz);
-        } else {
-            // speed-weighted Maxwellian: |c|^2 / s^2 ~ Gamma(2, 1), isotropic
-            const float y = -__logf(u01f(B.x)) - __logf(u01f(B.y));
-            cmag = s * sqrt_fast(y);
+            float sn0, cs0;
+            sincos_2pi(u01f(A.w), sn0, cs0);
+            f = cs0 * cs0;
+        }
+        const float y = -__logf(u01f(B.x)) - __logf(u01f(B.y)) * f;
+        const float cmag = s * sqrt_fast(y);
+        float cx, cy, cz;
+        {
             const float ct = 2.0f * u01f(B.z) - 1.0f;
             const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
             float sn, cs;
@@ -271,43 +267,18 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
     return __reduce_add_sync(0xffffffffu, v);
 }
 
-} // namespace
-
-// grid.x = total tiles over all instances (tile = blockDim.x packs);
-// tile_start[i] = first tile of instance i, tile_start[n_inst] = total.
-__global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 *insts,
-                                                       const int32_t *tile_start, int n_inst,
-                                                       int nsteps)
+// Advance the `blockDim.x` packs of one tile of instance P starting at pack
+// `off` by `nsteps` micro steps, and add the warp totals to the counters.
+template <bool kCollide>
+__device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, const float *s_rf,
+                                         int64_t off, int nsteps)
 {
-    extern __shared__ float s_rf[];
-    __shared__ InstF32 P;
-    __shared__ int64_t s_off;
-    const int b = blockIdx.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n_inst - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tile_start[mid] <= b) lo = mid;
-            else hi = mid - 1;
-        }
-        P = insts[lo];
-        s_off = (int64_t)(b - tile_start[lo]) * blockDim.x;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nsteps; k += blockDim.x) {
-        float v = 0.0f;
-        if (P.v_rf != 0.0 && P.dtf != 0.0) {
-            const double x = (double)(P.step0 + k) * P.dtf;
-            v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
-        }
-        s_rf[k] = v;
-    }
-    __syncthreads();
-    const int64_t p = s_off + threadIdx.x;
+    const int64_t p = off + threadIdx.x;
     unsigned n_steps_done = 0, n_coll = 0, n_ovf = 0;
     if (p < P.n_slots && P.status[p] == MUCITE_ACTIVE) {
         int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
         float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
+        float lnsy = P.tst ? P.lnsy[p] : 0.0f;
         const uint32_t pack = (uint32_t)p;
         float fx = (float)xq, fy = (float)yq;
         float rr = lattice_r(fx, fy);
@@ -318,11 +289,19 @@ __global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
             gather(G, P, fx, fy, rr, zq, L);
-            int ovf;
-            n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
-            n_ovf += ovf;
+            if (kCollide) {
+                int ovf;
+                n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
+                n_ovf += ovf;
+            }
             const float srf = s_rf[k];
             const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
+            if (P.tst) {
+                // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
+                const float Te = teff_of(P, eint);
+                const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
+                lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
+            }
             vx = add_sr(vx, P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx), dither(h1, 0));
             vy = add_sr(vy, P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy), dither(h1, 11));
             vz = add_sr(vz, P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz), dither(h1, 22));
@@ -342,6 +321,7 @@ __global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 
         P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
         P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
         P.eint[p] = eint;
+        if (P.tst) P.lnsy[p] = lnsy;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(P.step0 + k);
@@ -357,11 +337,90 @@ __global__ void __launch_bounds__(256) step_f32_kernel(GridF32 G, const InstF32 
     }
 }
 
-void launch_step_f32(const GridF32 &G, const InstF32 *d_insts, const int32_t *d_tile_start,
-                     int n_inst, int total_tiles, int threads, int nsteps, cudaStream_t s)
+} // namespace
+
+// Work list: tile t of the launch belongs to the instance i with
+// tile_start[i] <= t < tile_start[i + 1] (tile = blockDim.x packs). Block b
+// takes tiles b, b + gridDim.x, ... (one tile per block when the grid covers
+// the list; a persistent grid strides over it). Every thread finds its tile's
+// instance itself; the block copies the instance descriptor and its RF
+// scalars (rf_table_kernel) into shared memory only when the instance changes.
+template <bool kCollide>
+__global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF32 *insts,
+                                                       const int32_t *tile_start, int n_inst,
+                                                       int total_tiles, int nsteps)
 {
+    extern __shared__ float s_rf[];
+    __shared__ __align__(16) unsigned char p_raw[sizeof(InstF32)];
+    const InstF32 &P = *reinterpret_cast<const InstF32 *>(p_raw);
+    int cur = -1;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        int lo = 0, hi = n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&tile_start[mid]) <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {
+            __syncthreads(); // the previous tile's readers are done with P and s_rf
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + lo);
+            for (int w = threadIdx.x; w < (int)(sizeof(InstF32) / 4); w += blockDim.x)
+                reinterpret_cast<uint32_t *>(p_raw)[w] = src[w];
+            __syncthreads();
+            for (int k = threadIdx.x; k < nsteps; k += blockDim.x) s_rf[k] = P.rf[k];
+            __syncthreads();
+            cur = lo;
+        }
+        run_tile<kCollide>(G, P, s_rf, (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x, nsteps);
+    }
+}
+
+// RF scalar of Eq. 4 for the next `nsteps` steps of every instance: the
+// phase frac(n dt f) is taken in FP64 from the integer step count.
+__global__ void rf_table_kernel(const InstF32 *insts, int nsteps)
+{
+    const InstF32 &P = insts[blockIdx.x];
+    for (int k = threadIdx.x; k < nsteps; k += blockDim.x) {
+        float v = 0.0f;
+        if (P.v_rf != 0.0 && P.dtf != 0.0) {
+            const double x = (double)(P.step0 + k) * P.dtf;
+            v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
+        }
+        P.rf[k] = v;
+    }
+}
+
+// Instance clocks advanced on the device (graph replays).
+__global__ void advance_clock_kernel(InstF32 *insts, int n_inst, int nsteps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) insts[i].step0 += nsteps;
+}
+
+void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
+                     int total_tiles, int threads, int nsteps, int grid, bool collide, cudaStream_t s)
+{
+    rf_table_kernel<<<n_inst, 128, 0, s>>>(d_insts, nsteps);
     const size_t smem = sizeof(float) * (size_t)nsteps;
-    step_f32_kernel<<<total_tiles, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, nsteps);
+    if (collide)
+        step_f32_kernel<true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+    else
+        step_f32_kernel<false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+}
+
+void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)
+{
+    advance_clock_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(d_insts, n_inst, nsteps);
+}
+
+int step_f32_blocks_per_sm(int threads, int nsteps, bool collide)
+{
+    int b = 0;
+    if (collide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true>, threads, sizeof(float) * (size_t)nsteps);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false>, threads, sizeof(float) * (size_t)nsteps);
+    return b;
 }
 
 } // namespace mucite

@@ -107,18 +107,15 @@ __device__ int collide_d(const InstF64 &P, const LocalD &L, uint32_t pack, uint3
         if (t >= P.dt) return acc;
         double b[4], cp[3], cmag;
         draw(P, pack, step, 3u * k + 1u, b);
+        // |c'|^2 / s^2 ~ Gamma(3/2) (Maxwellian) or Gamma(2) (speed-weighted)
+        double fk = 1.0;
         if (a[1] * (w + cbar) < w) {
-            const double r01 = sqrt(-2.0 * log(b[0])), r23 = sqrt(-2.0 * log(b[2]));
-            const double sd = s / sqrt(2.0);
-            double sn, cs;
-            sincospi(2.0 * b[1], &sn, &cs);
-            cp[0] = sd * r01 * cs;
-            cp[1] = sd * r01 * sn;
-            cp[2] = sd * r23 * cospi(2.0 * b[3]);
-            cmag = sqrt(cp[0] * cp[0] + cp[1] * cp[1] + cp[2] * cp[2]);
-        } else {
-            const double y = -log(b[0]) - log(b[1]);
-            cmag = s * sqrt(y);
+            const double cw = cospi(2.0 * a[3]);
+            fk = cw * cw;
+        }
+        const double y = -log(b[0]) - log(b[1]) * fk;
+        cmag = s * sqrt(y);
+        {
             const double ct = 2.0 * b[2] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
             double sn, cs;
             sincospi(2.0 * b[3], &sn, &cs);
@@ -193,11 +190,17 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
         double x = P.x[p], y = P.y[p], z = P.z[p];
         double v[3] = {P.vx[p], P.vy[p], P.vz[p]};
         double eint = P.eint[p];
+        double lnsy = P.tst ? P.lnsy[p] : 0.0;
         LocalD L;
         gather_d(G, P, x, y, z, L);
         int ovf;
         coll = (unsigned)collide_d(P, L, (uint32_t)p, (uint32_t)step, v, eint, ovf);
         ovf_n = (unsigned)ovf;
+        if (P.tst) {
+            // Eq. 7: ln SY decays at the Eyring rate of the current T_eff
+            const double Te = teff_d(P.prof, eint);
+            lnsy -= P.tst_a * Te * exp(-P.tst_b / Te) * P.dt;
+        }
         for (int d = 0; d < 3; ++d)
             v[d] += P.qm * (P.dc_scale * L.ed[d] + srf * L.er[d] + L.es[d]) * P.dt;
         x += v[0] * P.dt;
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
         P.x[p] = x; P.y[p] = y; P.z[p] = z;
         P.vx[p] = v[0]; P.vy[p] = v[1]; P.vz[p] = v[2];
         P.eint[p] = eint;
+        if (P.tst) P.lnsy[p] = lnsy;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(step + 1);

@@ -51,11 +51,12 @@ __device__ __forceinline__ double teff_exact(const Profile &pf, double eint)
 __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
 {
     __shared__ unsigned long long s_cnt[8];
-    __shared__ double s_ke[8], s_te[8];
+    __shared__ double s_ke[8], s_te[8], s_sy[8];
     if (threadIdx.x < 8) {
         s_cnt[threadIdx.x] = 0;
         s_ke[threadIdx.x] = 0.0;
         s_te[threadIdx.x] = 0.0;
+        s_sy[threadIdx.x] = 0.0;
     }
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
         const int st = A.status[p];
         if (st < 8) {
             int32_t xq, yq, zq;
-            double vx, vy, vz, ei;
+            double vx, vy, vz, ei, ls;
             if (A.precision == MUCITE_FP32) {
                 xq = ((const int32_t *)A.x)[p];
                 yq = ((const int32_t *)A.y)[p];
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
                 vy = ((const float *)A.vy)[p];
                 vz = ((const float *)A.vz)[p];
                 ei = ((const float *)A.eint)[p];
+                ls = ((const float *)A.lnsy)[p];
             } else {
                 xq = q32t(__dmul_rn(((const double *)A.x)[p], A.sx));
                 yq = q32t(__dmul_rn(((const double *)A.y)[p], A.sx));
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
                 vy = ((const double *)A.vy)[p];
                 vz = ((const double *)A.vz)[p];
                 ei = ((const double *)A.eint)[p];
+                ls = ((const double *)A.lnsy)[p];
             }
             double v2 = __dmul_rn(vx, vx);
             v2 = __dadd_rn(v2, __dmul_rn(vy, vy));
@@ -90,6 +93,7 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
             atomicAdd(&s_cnt[st], 1ull);
             atomicAdd(&s_ke[st], W * ke);
             atomicAdd(&s_te[st], W * te);
+            atomicAdd(&s_sy[st], W * exp(ls));
             const float fx = (float)xq, fy = (float)yq;
             const float rr = __fsqrt_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)));
             const unsigned long long Wu = (unsigned long long)A.weight;
@@ -115,6 +119,7 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
         atomicAdd(&A.wsum[st], s_cnt[st] * (unsigned long long)A.weight);
         atomicAdd(&A.sum_ke[st], s_ke[st]);
         atomicAdd(&A.sum_teff[st], s_te[st]);
+        atomicAdd(&A.sum_sy[st], s_sy[st]);
     }
 }
 

@@ -22,7 +22,7 @@ MAX_INSTANCES = 256
 
 EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_fields",
            "mucite_state_layout", "mucite_inject", "mucite_release", "mucite_resume", "mucite_step",
-           "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning",
+           "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc"]
 
 
@@ -40,7 +40,7 @@ class Grid(C.Structure):
 class IonTemplate(C.Structure):
     _fields_ = [("mass_da", C.c_double), ("charge", C.c_int32), ("ccs_m2", C.c_double),
                 ("n_atoms", C.c_double), ("cv_c0", C.c_double), ("cv_c1", C.c_double),
-                ("T_init", C.c_double)]
+                ("T_init", C.c_double), ("dH_kJmol", C.c_double), ("dS_JmolK", C.c_double)]
 
 
 class Source(C.Structure):
@@ -62,7 +62,7 @@ class Run(C.Structure):
 
 class Layout(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("off_x", "off_y", "off_z", "off_vx", "off_vy", "off_vz",
-                                         "off_eint", "off_status", "off_t_term", "total_bytes")] + \
+                                         "off_eint", "off_status", "off_t_term", "off_lnsy", "total_bytes")] + \
                [("pos_bytes", C.c_int32), ("vel_bytes", C.c_int32)]
 
 
@@ -71,7 +71,7 @@ _i64p = C.POINTER(C.c_int64)
 
 class TallyOut(C.Structure):
     _fields_ = [("count", C.c_int64 * 8), ("weight", C.c_int64 * 8), ("sum_w_ke", C.c_double * 8),
-                ("sum_w_teff", C.c_double * 8), ("emitted_count", C.c_int64),
+                ("sum_w_teff", C.c_double * 8), ("sum_w_sy", C.c_double * 8), ("emitted_count", C.c_int64),
                 ("emitted_weight", C.c_int64), ("pack_steps", C.c_int64), ("collisions", C.c_int64),
                 ("candidate_overflow", C.c_int64), ("step", C.c_int64), ("exit_hist", _i64p),
                 ("r_hist", _i64p), ("ke_hist", _i64p), ("teff_hist", _i64p), ("loss_map", _i64p)]
@@ -105,6 +105,7 @@ def lib():
         L.mucite_tally.argtypes = [vp, C.c_int, C.POINTER(TallyOut)]
         L.mucite_pic_read.argtypes = [vp, C.c_int, _i64p, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), dp]
         L.mucite_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        L.mucite_set_launch_mode.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_launch_count.argtypes = [vp]
         L.mucite_launch_count.restype = C.c_int64
         L.mucite_sync.argtypes = [vp]
@@ -124,7 +125,7 @@ def grid_struct(g):
 
 def ion_struct(ion):
     return IonTemplate(ion.mass_da, int(ion.charge), ion.ccs_m2, float(ion.n_atoms), ion.cv_c0, ion.cv_c1,
-                       ion.T_init)
+                       ion.T_init, ion.dH_kJmol, ion.dS_JmolK)
 
 
 def source_struct(src):
@@ -235,6 +236,7 @@ class Context:
         out["weight"] = np.array(T.weight[:], np.int64)
         out["sum_w_ke"] = np.array(T.sum_w_ke[:])
         out["sum_w_teff"] = np.array(T.sum_w_teff[:])
+        out["sum_w_sy"] = np.array(T.sum_w_sy[:])
         for k in ("emitted_count", "emitted_weight", "pack_steps", "collisions", "candidate_overflow", "step"):
             out[k] = int(getattr(T, k))
         return out
@@ -255,6 +257,9 @@ class Context:
 
     def set_tuning(self, steps_per_launch=0, threads_per_block=0):
         self._check(lib().mucite_set_tuning(self._p, int(steps_per_launch), int(threads_per_block)))
+
+    def set_launch_mode(self, persistent_blocks_per_sm=0, use_graphs=True):
+        self._check(lib().mucite_set_launch_mode(self._p, int(persistent_blocks_per_sm), int(bool(use_graphs))))
 
     def launch_count(self):
         return int(lib().mucite_launch_count(self._p))
@@ -278,7 +283,7 @@ class Context:
         return dict(x=v(L.off_x, cap * ps, pt), y=v(L.off_y, cap * ps, pt), z=v(L.off_z, cap * ps, pt),
                     vx=v(L.off_vx, cap * vs, vt), vy=v(L.off_vy, cap * vs, vt), vz=v(L.off_vz, cap * vs, vt),
                     eint=v(L.off_eint, cap * vs, vt), status=v(L.off_status, cap, torch.uint8),
-                    t_term=v(L.off_t_term, cap * 4, torch.int32))
+                    t_term=v(L.off_t_term, cap * 4, torch.int32), lnsy=v(L.off_lnsy, cap * vs, vt))
 
 
 def poisson_solve_noalloc(device, stream, pic, Q, phi, esc, rel=None):

@@ -78,6 +78,9 @@ class IonTemplate:
     cv_c0: float = 1.0
     cv_c1: float = 0.0
     T_init: float = 300.0
+    # transition-state parameters of Eq. 7 (dH <= 0: no dissociation)
+    dH_kJmol: float = 0.0
+    dS_JmolK: float = 0.0
 
 
 @dataclasses.dataclass

@@ -1,0 +1,119 @@
+"""Batched stepping: many instances (different operating points, pack
+counts, seeds and clocks) advanced in one fused launch per chunk -- with the
+space-charge macro step batched over instances, CUDA-graph replay of whole
+macro steps and the persistent launch -- must give exactly the state each
+instance reaches when stepped alone. Per-pack arithmetic does not depend on
+the other packs in the launch, so the comparison is bit-exact."""
+import numpy as np
+import pytest
+
+from paper_2609_31258_b300 import workloads as W
+from helpers import download
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    from paper_2609_31258_b300 import build, mucite
+    build.build()
+    return mucite
+
+
+def _ring(n, seed, v_rf, dc, p_scale):
+    w = W.ring_stack(n_packs=n, n_steps=0, seed=seed, precision=0, nr=129, nz=513)
+    w.run.v_rf, w.run.dc_scale, w.run.p_scale = v_rf, dc, p_scale
+    return w
+
+
+POINTS = [(1500, 100, 50.0, 0.5, 0.5), (3333, 101, 150.0, 4.0, 2.0), (257, 102, 100.0, 2.0, 1.0)]
+
+
+def _alone(mc, w, steps, spl=64):
+    ctx = mc.Context(0)
+    ctx.set_tuning(spl, 128)
+    ctx.set_launch_mode(0, False)
+    mc.load_workload(ctx, w, 0)
+    for s in steps:
+        ctx.step(0, s)
+    out = download(ctx, 0, w.source.n_initial)
+    T = ctx.tally(0)
+    ctx.close()
+    return out, T
+
+
+@pytest.mark.parametrize("persistent,graphs", [(0, False), (0, True), (2, True)])
+def test_batched_equals_alone(mc, persistent, graphs):
+    import torch
+    ws = [_ring(*p) for p in POINTS]
+    ctx = mc.Context(0, torch.cuda.Stream())
+    ctx.set_tuning(64, 128)
+    ctx.set_launch_mode(persistent, graphs)
+    ctx.load_fields(ws[0].fields)
+    for i, w in enumerate(ws):
+        ctx.inject(i, w.ion, w.source, w.run)
+    ctx.step(-1, 700)
+    ctx.step(-1, 333)
+    if graphs:
+        assert ctx.launch_count() > 0
+    for i, w in enumerate(ws):
+        got = download(ctx, i, w.source.n_initial)
+        ref, Tref = _alone(mc, w, [700, 333])
+        for k in ref:
+            assert (got[k] == ref[k]).all(), (i, k)
+        T = ctx.tally(i)
+        assert T["pack_steps"] == Tref["pack_steps"] and T["collisions"] == Tref["collisions"]
+    ctx.close()
+
+
+def test_batched_mixed_clocks(mc):
+    """An instance admitted later (different clock) batched with running ones."""
+    ws = [_ring(*p) for p in POINTS[:2]]
+    ctx = mc.Context(0)
+    ctx.set_tuning(100, 128)
+    ctx.load_fields(ws[0].fields)
+    ctx.inject(0, ws[0].ion, ws[0].source, ws[0].run)
+    ctx.step(-1, 450)
+    ctx.inject(1, ws[1].ion, ws[1].source, ws[1].run)
+    ctx.step(-1, 500)
+    a = download(ctx, 0, ws[0].source.n_initial)
+    b = download(ctx, 1, ws[1].source.n_initial)
+    ra, _ = _alone(mc, ws[0], [950])
+    rb, _ = _alone(mc, ws[1], [500])
+    for k in ra:
+        assert (a[k] == ra[k]).all(), k
+        assert (b[k] == rb[k]).all(), k
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batched_space_charge(mc, graphs):
+    def cyl(n, seed, weight):
+        w = W.cylinder_space_charge(n_packs=n, n_steps=0, seed=seed, precision=0, pic_nr=65, pic_nz=257)
+        w.source.current_A = 0.0
+        w.source.weight = weight
+        return w
+    import torch
+    ws = [cyl(3000, 7, 20000), cyl(1000, 8, 5000), cyl(4500, 9, 1000)]
+    ctx = mc.Context(0, torch.cuda.Stream())
+    ctx.set_tuning(64, 128)
+    ctx.set_launch_mode(0, graphs)
+    ctx.load_fields(ws[0].fields)
+    for i, w in enumerate(ws):
+        ctx.inject(i, w.ion, w.source, w.run)
+    ctx.step(-1, 300)
+    for i, w in enumerate(ws):
+        got = download(ctx, i, w.source.n_initial)
+        pic = ctx.pic_read(i)
+        c1 = mc.Context(0)
+        c1.set_launch_mode(0, False)
+        c1.set_tuning(64, 128)
+        mc.load_workload(c1, w, 0)
+        c1.step(0, 300)
+        ref = download(c1, 0, w.source.n_initial)
+        pref = c1.pic_read(0)
+        c1.close()
+        for k in ref:
+            assert (got[k] == ref[k]).all(), (i, k)
+        assert (pic["Q"] == pref["Q"]).all()
+        assert np.abs(pic["phi"] - pref["phi"]).max() <= 1e-12 * max(np.abs(pref["phi"]).max(), 1e-30)
+    ctx.close()
