@@ -244,15 +244,21 @@ def main():
 
     # kernel-level roofline of the fused step kernel: launches of one step
     launches_per_step = launches_step / args.steps
-    kern_ms = t_ms / args.steps / max(launches_per_step, 1)
+    # each fused launch is preceded by the RF-table pre-kernel (~20 us of the
+    # ~14 ms; 0.15 % of the launch list), so the step kernel's average
+    # duration is the step time over the fused launches of one step
+    spl = args.spl or 2000
+    step_launches = -(-args.micro // spl)
+    kern_ms = t_ms / args.steps / step_launches
     insts = _inst_per_pack_step()
     sm_mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     peak_ginst = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9  # lane-instructions/s, in G
-    ach = (value / ws) * insts / 1e9 if insts else None
+    ps_per_launch = pack_steps / (args.steps * step_launches)
+    ach = insts * ps_per_launch / (kern_ms * 1e-3) / 1e9 if insts else None
     roofline = {"bound": "alu", "achieved": ach, "peak": peak_ginst, "unit": "Ginst/s (thread instructions)",
                 "frac": (ach / peak_ginst) if ach else None, "traffic": _traffic_per_launch(),
                 "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
-                "inst_per_pack_step": insts,
+                "inst_per_pack_step": insts, "pack_steps_per_launch": ps_per_launch,
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
                 "hbm_bytes_per_pack_step_at_launch": 57.0 / (args.spl or 2000)}
 

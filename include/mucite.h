@@ -115,6 +115,15 @@ typedef struct {
     int32_t pic_interval; /* steps between space-charge updates, 0 = none */
     int32_t exit_bin_steps, n_exit_bins, n_r_bins, n_ke_bins, n_teff_bins, n_loss_r, n_loss_z;
     double ke_max_ev, teff_max;
+    /* Hybrid Langevin branch (Methods, "optional hybrid Langevin branch";
+     * Table S2: switch at lambda dt >= 0.05): with langevin != 0, a pack in
+     * z in [lv_z0, lv_z1] whose expected collision rate satisfies
+     * lambda dt >= lv_switch gets an exact Ornstein-Uhlenbeck update of its
+     * velocity relative to the gas flow (friction q/(M K), Mason-Schamp
+     * mobility K) instead of explicit collisions; T_eff and the survival yield
+     * are not updated in that step. */
+    int32_t langevin;
+    double lv_z0, lv_z1, lv_switch;
 } mucite_run;
 
 /* Byte offsets of the structure-of-arrays pack pool (each array 256-byte

@@ -84,7 +84,8 @@ class OrcRun(C.Structure):
     _fields_ = [("dt", C.c_double), ("v_rf", C.c_double), ("f_rf", C.c_double),
                 ("phi_rf", C.c_double), ("dc_scale", C.c_double), ("p_scale", C.c_double),
                 ("hit_dist", C.c_double), ("z_exit", C.c_double), ("r_det", C.c_double),
-                ("m_gas_da", C.c_double), ("seed", C.c_uint64)]
+                ("m_gas_da", C.c_double), ("seed", C.c_uint64), ("langevin", C.c_int),
+                ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double)]
 
 
 class OrcState(C.Structure):
@@ -177,7 +178,8 @@ def ion_struct(ion):
 
 def run_struct(run):
     return OrcRun(run.dt, run.v_rf, run.f_rf, run.phi_rf, run.dc_scale, run.p_scale, run.hit_dist,
-                  run.z_exit, run.r_det, run.m_gas_da, run.seed & 0xFFFFFFFFFFFFFFFF)
+                  run.z_exit, run.r_det, run.m_gas_da, run.seed & 0xFFFFFFFFFFFFFFFF, int(run.langevin),
+                  run.lv_z0, run.lv_z1, run.lv_switch)
 
 
 def source_struct(src):

@@ -126,6 +126,8 @@ typedef struct {
 typedef struct {
     double dt, v_rf, f_rf, phi_rf, dc_scale, p_scale, hit_dist, z_exit, r_det, m_gas_da;
     uint64_t seed;
+    int langevin;                    /* hybrid Langevin branch on */
+    double lv_z0, lv_z1, lv_switch;  /* axial window and lambda*dt threshold */
 } orc_run;
 
 typedef struct {
@@ -360,6 +362,50 @@ static int collide(const orc_ion *ion, const orc_run *run, const orc_local *L, u
     return accepted;
 }
 
+/* Expected collision rate n sigma <|v - c|> of Eq. 6 with c drawn from the
+ * local Maxwellian about the flow: n sigma s [(x + 1/(2x)) erf(x) +
+ * exp(-x^2)/sqrt(pi)], x = |v - u|/s, s = sqrt(2kT/m_g) (-> 2s/sqrt(pi) at
+ * x = 0). Pinned: frozen-ion rate tests. */
+double orc_collision_rate(const orc_ion *ion, const orc_run *run, const orc_local *L, const double v[3])
+{
+    if (!(L->n > 0.0) || !(ion->ccs_m2 > 0.0) || !(L->T > 0.0)) return 0.0;
+    double mg = run->m_gas_da * ORC_DALTON;
+    double s = sqrt(2.0 * ORC_KB * L->T / mg);
+    double w = sqrt((v[0] - L->u[0]) * (v[0] - L->u[0]) + (v[1] - L->u[1]) * (v[1] - L->u[1]) +
+                    (v[2] - L->u[2]) * (v[2] - L->u[2]));
+    double x = w / s;
+    double gbar = x > 1e-6 ? s * ((x + 0.5 / x) * erf(x) + exp(-x * x) / sqrt(ORC_PI))
+                           : 2.0 * s / sqrt(ORC_PI);
+    return L->n * ion->ccs_m2 * gbar;
+}
+
+/* Hybrid Langevin branch ("optional hybrid Langevin branch ... aggregated
+ * velocity relaxation toward the local gas velocity plus a temperature
+ * dependent stochastic component"): exact Ornstein-Uhlenbeck update of the
+ * velocity relative to the flow over dt,
+ *   v <- u + (v - u) e^{-gamma dt} + sqrt(kT/M (1 - e^{-2 gamma dt})) xi,
+ * with the friction gamma = q / (M K) from the low-field Mason-Schamp
+ * mobility K = (3q / 16N) sqrt(2 pi / (mu k T)) / sigma. Normals from draw
+ * block 128 of the step (Box-Muller). T_eff is not updated. Pinned:
+ * stationary Maxwellian, drift K E, explicit-vs-hybrid transmission. */
+static void langevin_step(const orc_ion *ion, const orc_run *run, const orc_local *L, uint64_t seed,
+                          uint32_t pack, uint32_t step, double v[3])
+{
+    double M = ion->mass_da * ORC_DALTON, mg = run->m_gas_da * ORC_DALTON;
+    double mu = M * mg / (M + mg);
+    double q = fabs((double)ion->charge) * ORC_E_CHARGE;
+    double K = 3.0 * q / (16.0 * L->n) * sqrt(2.0 * ORC_PI / (mu * ORC_KB * L->T)) / ion->ccs_m2;
+    double gamma = q / (M * K);
+    double decay = exp(-gamma * run->dt);
+    double sd = sqrt(ORC_KB * L->T / M * -expm1(-2.0 * gamma * run->dt));
+    double u[4];
+    draw4(seed, pack, step, 128u, 0u, u);
+    double r01 = sqrt(-2.0 * log(u[0])), r23 = sqrt(-2.0 * log(u[2]));
+    double xi[3] = {r01 * cos(2.0 * ORC_PI * u[1]), r01 * sin(2.0 * ORC_PI * u[1]),
+                    r23 * cos(2.0 * ORC_PI * u[3])};
+    for (int d = 0; d < 3; ++d) v[d] = L->u[d] + (v[d] - L->u[d]) * decay + sd * xi[d];
+}
+
 /* Fixed-point lattice used for every discrete decision (classification, mask
  * lookup, deposit, tally bins): x = xq*R*2^-30, y likewise,
  * z = z0 + zq*(z1-z0)*2^-30. FP64 positions are quantised by rint(x*2^30/R). */
@@ -455,14 +501,21 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
             int64_t n = step0 + k;
             orc_local L;
             gather(F, run, x, y, z, &L);
-            int ovf = 0;
-            int nc = collide(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v, &eint,
+            int ovf = 0, nc = 0;
+            int lv = run->langevin && z >= run->lv_z0 && z <= run->lv_z1 &&
+                     orc_collision_rate(ion, run, &L, v) * run->dt >= run->lv_switch;
+            if (lv)
+                langevin_step(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v);
+            else
+                nc = collide(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v, &eint,
                              frozen_collisions, &ovf);
             if (S->ncoll) S->ncoll[p] += nc;
             if (S->noverflow) S->noverflow[p] += ovf;
             if (S->nsteps) S->nsteps[p] += 1;
-            /* Eq. 7: the survival yield decays at the rate of the current T_eff */
-            if (ion->dH_kJmol > 0.0) lnsy -= orc_eyring_rate(ion, orc_T_of_eint(ion, eint)) * run->dt;
+            /* Eq. 7: the survival yield decays at the rate of the current T_eff
+             * (not updated during an aggregated Langevin step) */
+            if (ion->dH_kJmol > 0.0 && !lv)
+                lnsy -= orc_eyring_rate(ion, orc_T_of_eint(ion, eint)) * run->dt;
             for (int d = 0; d < 3; ++d)
                 v[d] += qm * (run->dc_scale * L.Edc[d] + srf[k] * L.Erf[d] + L.Esc[d]) * run->dt;
             x += v[0] * run->dt;

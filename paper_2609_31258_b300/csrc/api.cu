@@ -233,6 +233,12 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
         P.tst_a_dt = (float)(kKB / kPlanck * exp(ion.dS_JmolK / kR) * r.dt);
         P.tst_b = (float)(ion.dH_kJmol * 1000.0 / kR);
+        P.langevin = r.langevin ? 1 : 0;
+        P.lv_zq0 = (int64_t)ceil((r.lv_z0 - g.z0) / (g.z1 - g.z0) * kLat);
+        P.lv_zq1 = (int64_t)floor((r.lv_z1 - g.z0) / (g.z1 - g.z0) * kLat);
+        P.lv_switch = (float)r.lv_switch;
+        P.lv_c = (float)(16.0 / 3.0 * sqrt(mu * kKB / (2.0 * kPi)) / M);
+        P.lv_kM = (float)(kKB / M);
         P.v_rf = r.v_rf;
         P.dtf = r.dt * r.f_rf;
         P.phi_rf = r.phi_rf;
@@ -281,6 +287,11 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
         P.tst_a = kKB / kPlanck * exp(ion.dS_JmolK / kR);
         P.tst_b = ion.dH_kJmol * 1000.0 / kR;
+        P.langevin = r.langevin ? 1 : 0;
+        P.lv_z0 = r.lv_z0;
+        P.lv_z1 = r.lv_z1;
+        P.lv_switch = r.lv_switch;
+        P.q_abs = fabs((double)ion.charge) * kE;
         P.qm = ion.charge * kE / (ion.mass_da * kDa);
         P.dc_scale = r.dc_scale;
         P.dt = r.dt;
@@ -522,16 +533,19 @@ bool can_collide(const mucite_ctx *ctx, const Instance &I)
 int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int total_tiles, int chunk)
 {
     if (total_tiles <= 0) return 0;
-    bool collide = false;
-    for (const Instance *I : grp) collide = collide || can_collide(ctx, *I);
+    bool collide = false, extras = false;
+    for (const Instance *I : grp) {
+        collide = collide || can_collide(ctx, *I);
+        extras = extras || I->f32.tst || I->f32.langevin;
+    }
     int grid = total_tiles;
     if (ctx->persistent > 0) {
         const int per_sm =
-            std::min(ctx->persistent, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide)));
+            std::min(ctx->persistent, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide, extras)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
     }
     launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,
-                    chunk, grid, collide, ctx->stream);
+                    chunk, grid, collide, extras, ctx->stream);
     return 2;
 }
 

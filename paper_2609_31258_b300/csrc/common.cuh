@@ -103,6 +103,11 @@ struct InstF32 {
     float n3, inv_n3, c0, c1, tcap, ecap;
     int tst;                   // dissociation (Eq. 7) on
     float tst_a_dt, tst_b;     // k dt = tst_a_dt * T * exp(-tst_b / T)
+    int langevin;              // hybrid Langevin branch on
+    int64_t lv_zq0, lv_zq1;    // window on the z lattice
+    float lv_switch;           // lambda dt threshold
+    float lv_c;                // gamma = lv_c * (n sigma) * sqrt(T)
+    float lv_kM;               // k_B / M
     uint32_t key0, key1;
     int64_t zexit_q;           // first lattice z counted as crossed
     uint64_t rdet2;            // (floor(r_det / R * 2^30))^2
@@ -123,6 +128,9 @@ struct InstF64 {
     Profile prof;
     int tst;
     double tst_a, tst_b;       // k = tst_a * T * exp(-tst_b / T)
+    int langevin;
+    double lv_z0, lv_z1, lv_switch;
+    double q_abs;              // |q| e
     uint64_t seed;
     int64_t zexit_q, rdet_q;
     float hit;

@@ -38,9 +38,10 @@ void launch_inject(const InjectArgs &A, cudaStream_t s);
 void launch_tally(const TallyArgs &A, cudaStream_t s);
 // grid == total_tiles: one tile per block; a smaller grid strides over the tiles.
 void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
-                     int total_tiles, int threads, int nsteps, int grid, bool collide, cudaStream_t s);
+                     int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
+                     cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
-int step_f32_blocks_per_sm(int threads, int nsteps, bool collide);
+int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras);
 void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, cudaStream_t s);
 
 } // namespace mucite

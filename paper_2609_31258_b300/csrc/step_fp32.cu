@@ -232,6 +232,41 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
     return acc;
 }
 
+// Expected collision rate n sigma <|v - c|> (Eq. 6, Maxwellian partner):
+// n sigma s [(x + 1/(2x)) erf(x) + exp(-x^2)/sqrt(pi)], x = |v - u| / s.
+__device__ __forceinline__ float collision_rate(const InstF32 &P, const Local &L, float vx, float vy,
+                                                float vz)
+{
+    const float s = sqrt_fast(P.s_coef * L.T);
+    const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
+    const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    const float x = __fdividef(w, s);
+    const float g = x > 1e-3f ? s * ((x + __fdividef(0.5f, x)) * erff(x) + __expf(-x * x) * 0.5641895835f)
+                              : 1.1283791671f * s * (1.0f + x * x * (1.0f / 3.0f));
+    return L.nsig * g;
+}
+
+// Hybrid Langevin step: exact Ornstein-Uhlenbeck update of v - u over dt with
+// friction gamma = q / (M K) (Mason-Schamp K) and the gas temperature's
+// equilibrium spread; normals from draw block 128 of the step.
+__device__ __forceinline__ void langevin_step(const InstF32 &P, const Local &L, uint32_t pack,
+                                              uint32_t step, float &vx, float &vy, float &vz)
+{
+    const float sqT = sqrt_fast(L.T);
+    const float gdt = P.lv_c * L.nsig * sqT * P.dt;
+    const float decay = __expf(-gdt);
+    const float sd = sqT * sqrt_fast(P.lv_kM * -expm1f(-2.0f * gdt));
+    const uint4 U = philox10(make_uint4(pack, step, 128u, 0u), P.key0, P.key1);
+    const float r01 = sd * sqrt_fast(-2.0f * __logf(u01f(U.x)));
+    const float r23 = sd * sqrt_fast(-2.0f * __logf(u01f(U.z)));
+    float sn, cs, sn2, cs2;
+    sincos_2pi(u01f(U.y), sn, cs);
+    sincos_2pi(u01f(U.w), sn2, cs2);
+    vx = L.ux + (vx - L.ux) * decay + r01 * cs;
+    vy = L.uy + (vy - L.uy) * decay + r01 * sn;
+    vz = L.uz + (vz - L.uz) * decay + r23 * cs2;
+}
+
 // Lattice displacement of one step, floor(d + u) with a uniform dither u,
 // clamped to keep the int32 lattice from wrapping.
 __device__ __forceinline__ int32_t lattice_step(float d, float u)
@@ -269,7 +304,7 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
 
 // Advance the `blockDim.x` packs of one tile of instance P starting at pack
 // `off` by `nsteps` micro steps, and add the warp totals to the counters.
-template <bool kCollide>
+template <bool kCollide, bool kExtras>
 __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, const float *s_rf,
                                          int64_t off, int nsteps)
 {
@@ -278,7 +313,7 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
     if (p < P.n_slots && P.status[p] == MUCITE_ACTIVE) {
         int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
         float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
-        float lnsy = P.tst ? P.lnsy[p] : 0.0f;
+        float lnsy = (kExtras && P.tst) ? P.lnsy[p] : 0.0f;
         const uint32_t pack = (uint32_t)p;
         float fx = (float)xq, fy = (float)yq;
         float rr = lattice_r(fx, fy);
@@ -289,14 +324,21 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
             gather(G, P, fx, fy, rr, zq, L);
+            bool lv = false;
             if (kCollide) {
-                int ovf;
-                n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
-                n_ovf += ovf;
+                if (kExtras && P.langevin && zq >= P.lv_zq0 && zq <= P.lv_zq1 && L.nsig > 0.0f && L.T > 0.0f)
+                    lv = collision_rate(P, L, vx, vy, vz) * P.dt >= P.lv_switch;
+                if (lv) {
+                    langevin_step(P, L, pack, n, vx, vy, vz);
+                } else {
+                    int ovf;
+                    n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
+                    n_ovf += ovf;
+                }
             }
             const float srf = s_rf[k];
             const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
-            if (P.tst) {
+            if (kExtras && P.tst && !lv) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
                 const float Te = teff_of(P, eint);
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
@@ -321,7 +363,7 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
         P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
         P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
         P.eint[p] = eint;
-        if (P.tst) P.lnsy[p] = lnsy;
+        if (kExtras && P.tst) P.lnsy[p] = lnsy;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(P.step0 + k);
@@ -345,7 +387,7 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
 // the list; a persistent grid strides over it). Every thread finds its tile's
 // instance itself; the block copies the instance descriptor and its RF
 // scalars (rf_table_kernel) into shared memory only when the instance changes.
-template <bool kCollide>
+template <bool kCollide, bool kExtras>
 __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF32 *insts,
                                                        const int32_t *tile_start, int n_inst,
                                                        int total_tiles, int nsteps)
@@ -371,7 +413,7 @@ __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF
             __syncthreads();
             cur = lo;
         }
-        run_tile<kCollide>(G, P, s_rf, (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x, nsteps);
+        run_tile<kCollide, kExtras>(G, P, s_rf, (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x, nsteps);
     }
 }
 
@@ -397,15 +439,22 @@ __global__ void advance_clock_kernel(InstF32 *insts, int n_inst, int nsteps)
     if (i < n_inst) insts[i].step0 += nsteps;
 }
 
+// kCollide: the collision code is compiled in; kExtras: dissociation (Eq. 7)
+// and the hybrid Langevin branch are compiled in.
 void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
-                     int total_tiles, int threads, int nsteps, int grid, bool collide, cudaStream_t s)
+                     int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
+                     cudaStream_t s)
 {
     rf_table_kernel<<<n_inst, 128, 0, s>>>(d_insts, nsteps);
     const size_t smem = sizeof(float) * (size_t)nsteps;
-    if (collide)
-        step_f32_kernel<true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+    if (collide && extras)
+        step_f32_kernel<true, true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+    else if (collide)
+        step_f32_kernel<true, false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+    else if (extras)
+        step_f32_kernel<false, true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
     else
-        step_f32_kernel<false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+        step_f32_kernel<false, false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
 }
 
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)
@@ -413,13 +462,18 @@ void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t
     advance_clock_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(d_insts, n_inst, nsteps);
 }
 
-int step_f32_blocks_per_sm(int threads, int nsteps, bool collide)
+int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras)
 {
     int b = 0;
-    if (collide)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true>, threads, sizeof(float) * (size_t)nsteps);
+    const size_t smem = sizeof(float) * (size_t)nsteps;
+    if (collide && extras)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, true>, threads, smem);
+    else if (collide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, false>, threads, smem);
+    else if (extras)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, true>, threads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false>, threads, sizeof(float) * (size_t)nsteps);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false>, threads, smem);
     return b;
 }
 

@@ -150,6 +150,33 @@ __device__ int collide_d(const InstF64 &P, const LocalD &L, uint32_t pack, uint3
     return acc;
 }
 
+__device__ double collision_rate_d(const InstF64 &P, const LocalD &L, const double v[3])
+{
+    if (!(L.n > 0.0) || !(P.sigma > 0.0) || !(L.T > 0.0)) return 0.0;
+    const double s = sqrt(2.0 * kKB * L.T / P.mg);
+    const double w = sqrt((v[0] - L.u[0]) * (v[0] - L.u[0]) + (v[1] - L.u[1]) * (v[1] - L.u[1]) +
+                          (v[2] - L.u[2]) * (v[2] - L.u[2]));
+    const double x = w / s;
+    const double g = x > 1e-6 ? s * ((x + 0.5 / x) * erf(x) + exp(-x * x) / sqrt(kPi)) : 2.0 * s / sqrt(kPi);
+    return L.n * P.sigma * g;
+}
+
+__device__ void langevin_d(const InstF64 &P, const LocalD &L, uint32_t pack, uint32_t step, double v[3])
+{
+    const double mu = P.M * P.mg / (P.M + P.mg);
+    const double K = 3.0 * P.q_abs / (16.0 * L.n) * sqrt(2.0 * kPi / (mu * kKB * L.T)) / P.sigma;
+    const double gamma = P.q_abs / (P.M * K);
+    const double decay = exp(-gamma * P.dt);
+    const double sd = sqrt(kKB * L.T / P.M * -expm1(-2.0 * gamma * P.dt));
+    double u[4];
+    draw(P, pack, step, 128u, u);
+    const double r01 = sqrt(-2.0 * log(u[0])), r23 = sqrt(-2.0 * log(u[2]));
+    double sn, cs;
+    sincospi(2.0 * u[1], &sn, &cs);
+    const double xi[3] = {r01 * cs, r01 * sn, r23 * cospi(2.0 * u[3])};
+    for (int d = 0; d < 3; ++d) v[d] = L.u[d] + (v[d] - L.u[d]) * decay + sd * xi[d];
+}
+
 __device__ __forceinline__ int32_t q32(double v)
 {
     const double r = rint(v);
@@ -193,10 +220,13 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
         double lnsy = P.tst ? P.lnsy[p] : 0.0;
         LocalD L;
         gather_d(G, P, x, y, z, L);
-        int ovf;
-        coll = (unsigned)collide_d(P, L, (uint32_t)p, (uint32_t)step, v, eint, ovf);
+        int ovf = 0;
+        const bool lv = P.langevin && z >= P.lv_z0 && z <= P.lv_z1 &&
+                        collision_rate_d(P, L, v) * P.dt >= P.lv_switch;
+        if (lv) langevin_d(P, L, (uint32_t)p, (uint32_t)step, v);
+        else coll = (unsigned)collide_d(P, L, (uint32_t)p, (uint32_t)step, v, eint, ovf);
         ovf_n = (unsigned)ovf;
-        if (P.tst) {
+        if (P.tst && !lv) {
             // Eq. 7: ln SY decays at the Eyring rate of the current T_eff
             const double Te = teff_d(P.prof, eint);
             lnsy -= P.tst_a * Te * exp(-P.tst_b / Te) * P.dt;

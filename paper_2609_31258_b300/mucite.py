@@ -57,7 +57,8 @@ class Run(C.Structure):
                 ("seed", C.c_uint64), ("precision", C.c_int32), ("pic_interval", C.c_int32),
                 ("exit_bin_steps", C.c_int32), ("n_exit_bins", C.c_int32), ("n_r_bins", C.c_int32),
                 ("n_ke_bins", C.c_int32), ("n_teff_bins", C.c_int32), ("n_loss_r", C.c_int32),
-                ("n_loss_z", C.c_int32), ("ke_max_ev", C.c_double), ("teff_max", C.c_double)]
+                ("n_loss_z", C.c_int32), ("ke_max_ev", C.c_double), ("teff_max", C.c_double),
+                ("langevin", C.c_int32), ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double)]
 
 
 class Layout(C.Structure):
@@ -137,7 +138,8 @@ def run_struct(run):
     return Run(run.dt, run.v_rf, run.f_rf, run.phi_rf, run.dc_scale, run.p_scale, run.hit_dist, run.z_exit,
                run.r_det, run.m_gas_da, run.seed & 0xFFFFFFFFFFFFFFFF, run.precision, run.pic_interval,
                run.exit_bin_steps, run.n_exit_bins, run.n_r_bins, run.n_ke_bins, run.n_teff_bins,
-               run.n_loss_r, run.n_loss_z, run.ke_max_ev, run.teff_max)
+               run.n_loss_r, run.n_loss_z, run.ke_max_ev, run.teff_max, int(run.langevin), run.lv_z0, run.lv_z1,
+               run.lv_switch)
 
 
 def state_layout(precision, capacity):

@@ -113,6 +113,12 @@ class Run:
     seed: int = 0
     precision: int = 0        # 0 = FP32 fused path, 1 = plain FP64 path
     pic_interval: int = 0     # steps between PIC updates, 0 = no space charge
+    # hybrid Langevin branch: OU relaxation instead of explicit collisions in
+    # z in [lv_z0, lv_z1] where lambda*dt >= lv_switch (Table S2: 0.05)
+    langevin: int = 0
+    lv_z0: float = 0.0
+    lv_z1: float = 0.0
+    lv_switch: float = 0.05
     # tally histogram layout
     exit_bin_steps: int = 1000
     n_exit_bins: int = 64
