@@ -124,6 +124,16 @@ typedef struct {
      * are not updated in that step. */
     int32_t langevin;
     double lv_z0, lv_z1, lv_switch;
+    /* pic_masked != 0: the space-charge solve also imposes Phi = 0 on metal
+     * nodes of the PIC grid (the electrode mask at the nearest static node),
+     * by conjugate gradients preconditioned with the maskless fast solve
+     * (at most 200 iterations, same 1e-6 tolerance). */
+    int32_t pic_masked;
+    /* integrator 0: leapfrog (kick-drift, one field evaluation per step);
+     * 1: fourth-order Runge-Kutta under the instantaneous total field (the
+     * paper's pusher, "Particle transport, collisions, and effective internal
+     * temperature"): field evaluations at t, t + dt/2 (twice) and t + dt. */
+    int32_t integrator;
 } mucite_run;
 
 /* Byte offsets of the structure-of-arrays pack pool (each array 256-byte
@@ -243,6 +253,22 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
  * `threads_per_block` threads (a multiple of 32, <= 1024). 0 keeps the
  * current value. */
 mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block);
+
+/* Start a new dt segment of instance `instance` at its current step (the
+ * global micro step of Eq. 1 is chosen per macro step): the RF phase carries
+ * over continuously, the step count (and with it the random-number counters)
+ * continues. Errors: MUCITE_E_ARG (dt <= 0), MUCITE_E_STATE. */
+mucite_status mucite_set_dt(mucite_ctx *ctx, int instance, double dt);
+
+/* Limits of the global micro step of Eq. 1 on the instance's current state
+ * (synchronises the stream): out[0] = 0.05 t_RF, out[1] = 0.1 tau_coll
+ * (1 / largest expected collision rate of an active pack), out[2] = dt_acc =
+ * 0.1 min over packs of max(|v|, sqrt(kT/M)) / |q E_tot / M|, out[3] =
+ * dt_CFL = 0.5 min(dr, dz) / max |v|, out[4] = dt_L = 2 ns with the hybrid
+ * Langevin branch on (Table S2), out[5] = the smallest; +inf where a limit
+ * does not apply. dt_rem (time to the next scheduled boundary) is the
+ * caller's to add. Limits are evaluated in FP32 for both precisions. */
+mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
 
 /* Launch mode of the batched FP32 step (the paper runs independent cases as
  * separate processes, Supporting Information S6; here many instances share

@@ -85,7 +85,8 @@ class OrcRun(C.Structure):
                 ("phi_rf", C.c_double), ("dc_scale", C.c_double), ("p_scale", C.c_double),
                 ("hit_dist", C.c_double), ("z_exit", C.c_double), ("r_det", C.c_double),
                 ("m_gas_da", C.c_double), ("seed", C.c_uint64), ("langevin", C.c_int),
-                ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double)]
+                ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double),
+                ("integrator", C.c_int), ("rf_phase0", C.c_double), ("seg_step0", C.c_int64)]
 
 
 class OrcState(C.Structure):
@@ -121,6 +122,7 @@ def _declare(L):
     L.orc_efield_from_phi.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
     L.orc_rf_scalar.argtypes = [P(OrcRun), C.c_int64]
     L.orc_rf_scalar.restype = C.c_double
+    L.orc_dt_limits.argtypes = [P(OrcFields), P(OrcIon), P(OrcRun), P(OrcState), C.c_int64, C.c_int64, _dp]
     L.orc_quantize.argtypes = [C.c_double] * 6 + [_i32p, _i32p, _i32p]
     L.orc_classify_fixed.argtypes = [P(OrcFields), P(OrcRun), C.c_int64, _i32p, _i32p, _i32p, _u8p]
     L.orc_run_steps.argtypes = [P(OrcFields), P(OrcIon), P(OrcRun), P(OrcState), C.c_int64,
@@ -179,7 +181,8 @@ def ion_struct(ion):
 def run_struct(run):
     return OrcRun(run.dt, run.v_rf, run.f_rf, run.phi_rf, run.dc_scale, run.p_scale, run.hit_dist,
                   run.z_exit, run.r_det, run.m_gas_da, run.seed & 0xFFFFFFFFFFFFFFFF, int(run.langevin),
-                  run.lv_z0, run.lv_z1, run.lv_switch)
+                  run.lv_z0, run.lv_z1, run.lv_switch, int(run.integrator), float(getattr(run, "_rf_phase0", 0.0)),
+                  int(getattr(run, "_seg_step0", 0)))
 
 
 def source_struct(src):
@@ -357,12 +360,33 @@ class Sim:
         ("Axisymmetric PIC space charge update")."""
         from . import poisson
         Q = self.deposit()
-        phi = poisson.solve(self.pic, Q)
+        if getattr(self.run, "pic_masked", 0):
+            metal = poisson.pic_metal_from_static(self.g, self.w.fields.mask, self.pic)
+            phi = poisson.solve_masked(self.pic, Q, metal) if metal.any() else poisson.solve(self.pic, Q)
+        else:
+            phi = poisson.solve(self.pic, Q)
         self.phi_sc = phi
         er, ez = efield_from_phi(phi, self.pic.dr, self.pic.dz)
         self.er_sc[...] = er
         self.ez_sc[...] = ez
         return Q, phi
+
+    def set_dt(self, dt):
+        """Start a new dt segment at the current step: the RF phase carries
+        over (frac of the phase reached), the step clock continues."""
+        run = self.run
+        if run.f_rf > 0:
+            x = getattr(run, "_rf_phase0", 0.0) + (self.step - getattr(run, "_seg_step0", 0)) * (run.dt * run.f_rf)
+            run._rf_phase0 = x - np.floor(x)
+        run._seg_step0 = self.step
+        run.dt = dt
+
+    def dt_limits(self):
+        out = np.zeros(6)
+        lib().orc_dt_limits(C.byref(self.fields_struct()), C.byref(ion_struct(self.ion)),
+                            C.byref(run_struct(self.run)), C.byref(self.state_struct()), self.n, self.step,
+                            _ptr(out, _dp))
+        return out
 
     def advance(self, nsteps):
         """Advance nsteps with the PIC cycle every pic_interval steps and the

@@ -128,6 +128,9 @@ typedef struct {
     uint64_t seed;
     int langevin;                    /* hybrid Langevin branch on */
     double lv_z0, lv_z1, lv_switch;  /* axial window and lambda*dt threshold */
+    int integrator;                  /* 0 leapfrog, 1 RK4 */
+    double rf_phase0;                /* RF phase (cycles) at the start of the current dt segment */
+    int64_t seg_step0;               /* step count at the start of the current dt segment */
 } orc_run;
 
 typedef struct {
@@ -264,12 +267,30 @@ static void gather(const orc_fields *F, const orc_run *run, double x, double y, 
     }
 }
 
+/* Acceleration (q/m) E_tot at a position for a given RF scalar (Eq. 3, Eq. 4). */
+static void field_accel(const orc_fields *F, const orc_run *run, double qm, const double p[3], double srf,
+                        double a[3])
+{
+    orc_local L;
+    gather(F, run, p[0], p[1], p[2], &L);
+    for (int d = 0; d < 3; ++d) a[d] = qm * (run->dc_scale * L.Edc[d] + srf * L.Erf[d] + L.Esc[d]);
+}
+
 /* RF scalar V/Vref * cos(2 pi f t_n + phi) with t_n = n dt; the phase is the
  * fractional part of n*dt*f taken in FP64 (Eq. 4, Vref = 1 V). */
 double orc_rf_scalar(const orc_run *run, int64_t n)
 {
     if (run->v_rf == 0.0 || run->f_rf == 0.0) return 0.0;
-    double x = (double)n * (run->dt * run->f_rf);
+    double x = run->rf_phase0 + (double)(n - run->seg_step0) * (run->dt * run->f_rf);
+    double frac = x - floor(x);
+    return run->v_rf * cos(2.0 * ORC_PI * frac + run->phi_rf);
+}
+
+/* RF scalar half a step after step n (RK4 midpoint evaluations). */
+double orc_rf_scalar_half(const orc_run *run, int64_t n)
+{
+    if (run->v_rf == 0.0 || run->f_rf == 0.0) return 0.0;
+    double x = run->rf_phase0 + ((double)(n - run->seg_step0) + 0.5) * (run->dt * run->f_rf);
     double frac = x - floor(x);
     return run->v_rf * cos(2.0 * ORC_PI * frac + run->phi_rf);
 }
@@ -516,11 +537,30 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
              * (not updated during an aggregated Langevin step) */
             if (ion->dH_kJmol > 0.0 && !lv)
                 lnsy -= orc_eyring_rate(ion, orc_T_of_eint(ion, eint)) * run->dt;
-            for (int d = 0; d < 3; ++d)
-                v[d] += qm * (run->dc_scale * L.Edc[d] + srf[k] * L.Erf[d] + L.Esc[d]) * run->dt;
-            x += v[0] * run->dt;
-            y += v[1] * run->dt;
-            z += v[2] * run->dt;
+            if (run->integrator == 1) {
+                /* RK4 under the instantaneous total field (L38, L108): four field
+                 * evaluations at t_n, t_n + dt/2 (twice) and t_n + dt */
+                double h = run->dt, sh = orc_rf_scalar_half(run, n), s1 = orc_rf_scalar(run, n + 1);
+                double p[3] = {x, y, z}, a1[3], a2[3], a3[3], a4[3], v2[3], v3[3], v4[3], q[3];
+                field_accel(F, run, qm, p, srf[k], a1);
+                for (int d = 0; d < 3; ++d) { q[d] = p[d] + 0.5 * h * v[d]; v2[d] = v[d] + 0.5 * h * a1[d]; }
+                field_accel(F, run, qm, q, sh, a2);
+                for (int d = 0; d < 3; ++d) { q[d] = p[d] + 0.5 * h * v2[d]; v3[d] = v[d] + 0.5 * h * a2[d]; }
+                field_accel(F, run, qm, q, sh, a3);
+                for (int d = 0; d < 3; ++d) { q[d] = p[d] + h * v3[d]; v4[d] = v[d] + h * a3[d]; }
+                field_accel(F, run, qm, q, s1, a4);
+                for (int d = 0; d < 3; ++d) {
+                    p[d] += h / 6.0 * (v[d] + 2.0 * v2[d] + 2.0 * v3[d] + v4[d]);
+                    v[d] += h / 6.0 * (a1[d] + 2.0 * a2[d] + 2.0 * a3[d] + a4[d]);
+                }
+                x = p[0]; y = p[1]; z = p[2];
+            } else {
+                for (int d = 0; d < 3; ++d)
+                    v[d] += qm * (run->dc_scale * L.Edc[d] + srf[k] * L.Erf[d] + L.Esc[d]) * run->dt;
+                x += v[0] * run->dt;
+                y += v[1] * run->dt;
+                z += v[2] * run->dt;
+            }
             int32_t xq, yq, zq;
             orc_quantize(F->R, F->z0, F->z1, x, y, z, &xq, &yq, &zq);
             int st = classify_q(F, &thr, xq, yq, zq);
@@ -536,6 +576,48 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
         if (S->lnsy) S->lnsy[p] = lnsy;
     }
     free(srf);
+}
+
+/* Limits of the global micro step of Eq. 1 on the current state:
+ * out[0] = 0.05 t_RF, out[1] = 0.1 tau_coll (1 / largest expected collision
+ * rate), out[2] = dt_acc = 0.1 min_p max(|v|, v_th) / |a| (velocity change
+ * per step at most 10 % of the speed scale; v_th = sqrt(kT/M) of the local
+ * gas), out[3] = dt_CFL = 0.5 min(dr, dz) / max|v| (displacement at most half
+ * a grid spacing), out[4] = dt_L = 2 ns with the hybrid branch on (Table S2),
+ * out[5] = the smallest of them; absent limits are +inf. dt_rem, the time to
+ * the next scheduled boundary, is the caller's. */
+void orc_dt_limits(const orc_fields *F, const orc_ion *ion, const orc_run *run, const orc_state *S,
+                   int64_t n_packs, int64_t step, double out[6])
+{
+    double qm = ion->charge * ORC_E_CHARGE / (ion->mass_da * ORC_DALTON);
+    double M = ion->mass_da * ORC_DALTON;
+    double srf = orc_rf_scalar(run, step);
+    double lam = 0.0, vmax = 0.0, acc = INFINITY;
+    for (int64_t p = 0; p < n_packs; ++p) {
+        if (S->status[p] != ORC_ACTIVE) continue;
+        double v[3] = {S->vx[p], S->vy[p], S->vz[p]};
+        orc_local L;
+        gather(F, run, S->x[p], S->y[p], S->z[p], &L);
+        double r = orc_collision_rate(ion, run, &L, v);
+        if (r > lam) lam = r;
+        double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (vm > vmax) vmax = vm;
+        double a[3];
+        for (int d = 0; d < 3; ++d) a[d] = qm * (run->dc_scale * L.Edc[d] + srf * L.Erf[d] + L.Esc[d]);
+        double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        double vth = L.T > 0.0 ? sqrt(ORC_KB * L.T / M) : 0.0;
+        double vs = vm > vth ? vm : vth;
+        if (am > 0.0 && 0.1 * vs / am < acc) acc = 0.1 * vs / am;
+    }
+    double dr = F->R / (F->nr - 1), dz = (F->z1 - F->z0) / (F->nz - 1);
+    out[0] = run->f_rf > 0.0 && run->v_rf != 0.0 ? 0.05 / run->f_rf : INFINITY;
+    out[1] = lam > 0.0 ? 0.1 / lam : INFINITY;
+    out[2] = acc;
+    out[3] = vmax > 0.0 ? 0.5 * (dr < dz ? dr : dz) / vmax : INFINITY;
+    out[4] = run->langevin ? 2e-9 : INFINITY;
+    double m = out[0];
+    for (int i = 1; i < 5; ++i) if (out[i] < m) m = out[i];
+    out[5] = m;
 }
 
 /* Count accepted collisions in one step of length dt at a fixed ion velocity

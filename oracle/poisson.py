@@ -95,3 +95,46 @@ def residual(pic, Q, phi):
     x = np.asarray(phi)[1:-1, :-1].reshape(-1)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(b - A @ x) / (nb if nb > 0 else 1.0))
+
+
+def masked_matrix(pic, metal):
+    """Operator with Phi = 0 imposed at metal-mask nodes ("Zero perturbation
+    potential is imposed ... at metal mask nodes"): metal unknowns get the
+    identity row, and their coupling is removed from fluid rows (Phi_metal = 0
+    there). `metal` is a bool array [nz][nr]."""
+    A = fv_matrix(pic).tocsr()
+    m = np.asarray(metal)[1:-1, :-1].reshape(-1).astype(bool)
+    keep = sp.diags((~m).astype(np.float64))
+    Am = keep @ A @ keep + sp.diags(m.astype(np.float64))
+    return Am.tocsc(), m
+
+
+def solve_masked(pic, Q, metal):
+    """Phi [nz][nr] of the masked system, direct solve (zero on metal nodes
+    and on the Dirichlet boundary)."""
+    Am, m = masked_matrix(pic, metal)
+    b = rhs(pic, Q)
+    b[m] = 0.0
+    x = spla.splu(Am).solve(b)
+    phi = np.zeros((pic.nz, pic.nr))
+    phi[1:-1, :-1] = x.reshape(pic.nz - 2, pic.nr - 1)
+    return phi
+
+
+def residual_masked(pic, Q, phi, metal):
+    Am, m = masked_matrix(pic, metal)
+    b = rhs(pic, Q)
+    b[m] = 0.0
+    x = np.asarray(phi)[1:-1, :-1].reshape(-1)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(b - Am @ x) / (nb if nb > 0 else 1.0))
+
+
+def pic_metal_from_static(static_grid, static_mask, pic):
+    """Metal flag of each PIC node: the static-grid mask at the nearest static
+    node (both grids span the same box)."""
+    r = np.arange(pic.nr) * pic.dr
+    z = pic.z0 + np.arange(pic.nz) * pic.dz
+    i = np.clip(np.rint(r / static_grid.dr).astype(int), 0, static_grid.nr - 1)
+    j = np.clip(np.rint((z - static_grid.z0) / static_grid.dz).astype(int), 0, static_grid.nz - 1)
+    return np.asarray(static_mask)[np.ix_(j, i)] != 0

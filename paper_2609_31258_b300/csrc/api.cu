@@ -2,6 +2,7 @@
 // loading, instances (pack pools owned by the caller), stepping with the
 // space-charge macro step interleaved, tallies. All device work is enqueued
 // on the context stream; calls return a status and never throw.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -26,6 +27,8 @@ struct Instance {
     mucite_layout lay{};
     int64_t n_slots = 0;
     int64_t step = 0;
+    double rf_phase0 = 0.0;  // RF phase at the start of the current dt segment
+    int64_t seg_step0 = 0;   // step at the start of the current dt segment
     double src_acc = 0.0;
     unsigned long long *d_counters = nullptr; // [3]
     // tally buffers: [0..7] count, [8..15] wsum, then hist arrays; sums in d_tsum
@@ -33,6 +36,7 @@ struct Instance {
     double *d_tsum = nullptr; // [24]: sum_ke[8], sum_teff[8], sum_sy[8]
     int64_t tally_len = 0;
     bool has_pic = false;
+    bool pic_masked = false;
     PicInst pic{};
     InstF32 f32{};
     InstF64 f64{};
@@ -54,6 +58,9 @@ struct mucite_ctx {
     PicGeom pg{};
     float *d_S = nullptr, *d_cp = nullptr, *d_invm = nullptr, *d_lo = nullptr;
     double *d_a = nullptr, *d_c = nullptr, *d_A = nullptr;
+    uint8_t *d_pic_metal = nullptr; // metal flags of the PIC nodes
+    unsigned *d_limits = nullptr;   // Eq. 1 reduction scratch [3]
+    bool pic_has_metal = false;
     Instance inst[MUCITE_MAX_INSTANCES];
     InstF32 *d_insts = nullptr;
     int32_t *d_tiles = nullptr;
@@ -186,6 +193,10 @@ void free_instance(Instance &I)
     dfree(I.pic.ez64);
     dfree(I.pic.red);
     dfree(I.pic.conv);
+    dfree(I.pic.r64);
+    dfree(I.pic.z64);
+    dfree(I.pic.q64);
+    dfree(I.pic.p64);
     I = Instance();
 }
 
@@ -201,6 +212,8 @@ void free_fields(mucite_ctx *ctx)
     dfree(ctx->d_a);
     dfree(ctx->d_c);
     dfree(ctx->d_A);
+    dfree(ctx->d_pic_metal);
+    ctx->pic_has_metal = false;
     ctx->fields = false;
     ctx->has_pic_grid = false;
 }
@@ -217,9 +230,10 @@ void bind_params(mucite_ctx *ctx, Instance &I)
     const Profile pf = profile_of(ion);
     const int64_t zexit_q = (int64_t)ceil((r.z_exit - g.z0) / (g.z1 - g.z0) * kLat);
     const int64_t rdet_q = (int64_t)floor(r.r_det / g.R * kLat);
-    if (I.lay.pos_bytes == 4) {
+    {
         InstF32 &P = I.f32;
         P = InstF32{};
+        if (I.lay.pos_bytes == 4) {
         P.xq = at<int32_t>(I.pool, I.lay.off_x);
         P.yq = at<int32_t>(I.pool, I.lay.off_y);
         P.zq = at<int32_t>(I.pool, I.lay.off_z);
@@ -230,6 +244,10 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.status = at<uint8_t>(I.pool, I.lay.off_status);
         P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
         P.lnsy = at<float>(I.pool, I.lay.off_lnsy);
+        }
+        P.rk4 = r.integrator == 1 ? 1 : 0;
+        P.rf_phase0 = I.rf_phase0;
+        P.seg_step0 = I.seg_step0;
         P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
         P.tst_a_dt = (float)(kKB / kPlanck * exp(ion.dS_JmolK / kR) * r.dt);
         P.tst_b = (float)(ion.dH_kJmol * 1000.0 / kR);
@@ -271,7 +289,8 @@ void bind_params(mucite_ctx *ctx, Instance &I)
             P.psr = (float)(ctx->pg.pnr - 1) * (1.0f / 1073741824.0f);
         }
         P.counters = I.d_counters;
-    } else {
+    }
+    if (I.lay.pos_bytes == 8) {
         InstF64 &P = I.f64;
         P = InstF64{};
         P.x = at<double>(I.pool, I.lay.off_x);
@@ -292,6 +311,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.lv_z1 = r.lv_z1;
         P.lv_switch = r.lv_switch;
         P.q_abs = fabs((double)ion.charge) * kE;
+        P.rk4 = r.integrator == 1 ? 1 : 0;
         P.qm = ion.charge * kE / (ion.mass_da * kDa);
         P.dc_scale = r.dc_scale;
         P.dt = r.dt;
@@ -345,10 +365,13 @@ GridF64 grid_f64(const mucite_ctx *ctx)
     return G;
 }
 
-double rf_scalar(const mucite_run &r, int64_t n)
+// RF scalar of Eq. 4 at step n (plus `half` of a step) of the instance's
+// current dt segment: V cos(2 pi frac(phase0 + (n - seg0) dt f) + phi).
+double rf_scalar(const Instance &I, int64_t n, double half = 0.0)
 {
+    const mucite_run &r = I.run;
     if (r.v_rf == 0.0 || r.f_rf == 0.0) return 0.0;
-    const double x = (double)n * (r.dt * r.f_rf);
+    const double x = I.rf_phase0 + ((double)(n - I.seg_step0) + half) * (r.dt * r.f_rf);
     const double frac = x - floor(x);
     return r.v_rf * cos(2.0 * kPi * frac + r.phi_rf);
 }
@@ -429,8 +452,16 @@ DepositArgs deposit_args(const mucite_ctx *ctx, const Instance &I)
 }
 
 // Upload the descriptors of a space-charge group (outside any capture).
-mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, int &total_tiles)
+mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in, int &total_tiles,
+                         int &n_masked)
 {
+    // maskless instances first, mask-aware ones after: two batched solves
+    std::vector<Instance *> grp;
+    for (Instance *I : grp_in)
+        if (!I->pic_masked) grp.push_back(I);
+    for (Instance *I : grp_in)
+        if (I->pic_masked) grp.push_back(I);
+    n_masked = (int)std::count_if(grp_in.begin(), grp_in.end(), [](Instance *I) { return I->pic_masked; });
     const size_t n = grp.size();
     std::vector<DepositArgs> dep(n);
     std::vector<PicInst> pi(n);
@@ -453,20 +484,30 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, in
 
 // Space-charge macro step of a group: clear, deposit, solve, E_SCE -- a fixed
 // number of launches for any number of instances.
-int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles)
+int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
 {
     launch_pic_prepare(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
     launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
-    return 2 + launch_pic_solve(ctx->pg, ctx->d_picinst, n_inst, 8, 1e-6, ctx->stream);
+    int64_t l = 2;
+    const int n_plain = n_inst - n_masked;
+    if (n_plain > 0) l += launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, 8, 1e-6, ctx->stream);
+    if (n_masked > 0) {
+        PicGeom Gm = ctx->pg;
+        Gm.metal = ctx->d_pic_metal;
+        l += launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, 200, 1e-6, ctx->stream);
+        launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
+        l += 1;
+    }
+    return l;
 }
 
 mucite_status pic_update_group(mucite_ctx *ctx, const std::vector<Instance *> &grp)
 {
     if (grp.empty()) return MUCITE_OK;
-    int total = 0;
-    const mucite_status st = pic_upload(ctx, grp, total);
+    int total = 0, nm = 0;
+    const mucite_status st = pic_upload(ctx, grp, total, nm);
     if (st != MUCITE_OK) return st;
-    ctx->launches += pic_launch(ctx, (int)grp.size(), total);
+    ctx->launches += pic_launch(ctx, (int)grp.size(), total, nm);
     CKL();
     return MUCITE_OK;
 }
@@ -510,7 +551,7 @@ mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, i
         host[k] = I->f32;
         host[k].n_slots = I->n_slots;
         host[k].step0 = I->step;
-        host[k].rf = ctx->d_rf + k * (size_t)chunk;
+        host[k].rf = ctx->d_rf + k * (size_t)(2 * chunk + 1);
         tiles[k] = (int32_t)total;
         total += (I->n_slots + ctx->threads - 1) / ctx->threads;
     }
@@ -570,7 +611,7 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
         const int chunk = P0 > 0 ? P0 : ctx->steps_per_launch;
         const int64_t reps = (nsteps - done) / chunk;
         if (reps >= 2) {
-            mucite_status st = ensure_rf(ctx, n * (size_t)chunk);
+            mucite_status st = ensure_rf(ctx, n * (size_t)(2 * chunk + 1));
             if (st != MUCITE_OK) return st;
             std::vector<const void *> key;
             key.push_back((const void *)(intptr_t)chunk);
@@ -580,11 +621,11 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 key.push_back(I);
                 key.push_back((const void *)(intptr_t)I->n_slots);
             }
-            int tiles = 0, ptiles = 0;
+            int tiles = 0, ptiles = 0, pmasked = 0;
             st = step_upload(ctx, grp, chunk, tiles);
             if (st != MUCITE_OK) return st;
             if (P0 > 0) {
-                st = pic_upload(ctx, grp, ptiles);
+                st = pic_upload(ctx, grp, ptiles, pmasked);
                 if (st != MUCITE_OK) return st;
             }
             if (!ctx->graph || key != ctx->graph_key) {
@@ -592,7 +633,7 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                 int64_t l = 0;
-                if (P0 > 0) l += pic_launch(ctx, (int)n, ptiles);
+                if (P0 > 0) l += pic_launch(ctx, (int)n, ptiles, pmasked);
                 l += step_launch(ctx, grp, tiles, chunk);
                 launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
                 l += 1;
@@ -627,7 +668,7 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
         }
         mucite_status st = pic_update_group(ctx, due);
         if (st != MUCITE_OK) return st;
-        st = ensure_rf(ctx, n * (size_t)chunk);
+        st = ensure_rf(ctx, n * (size_t)(2 * chunk + 1));
         if (st != MUCITE_OK) return st;
         int tiles = 0;
         st = step_upload(ctx, grp, (int)chunk, tiles);
@@ -652,7 +693,8 @@ mucite_status step_f64_one(mucite_ctx *ctx, Instance &I, int64_t nsteps)
         }
         InstF64 p = I.f64;
         p.n_slots = I.n_slots;
-        launch_step_f64(G, p, I.step, rf_scalar(I.run, I.step), ctx->stream);
+        launch_step_f64(G, p, I.step, rf_scalar(I, I.step), rf_scalar(I, I.step, 0.5), rf_scalar(I, I.step + 1),
+                        ctx->stream);
         ctx->launches++;
         CKL();
         I.step += 1;
@@ -681,6 +723,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_picinst, sizeof(PicInst) * MUCITE_MAX_INSTANCES);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep, sizeof(DepositArgs) * MUCITE_MAX_INSTANCES);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_limits, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         fail(nullptr, MUCITE_E_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
@@ -689,6 +732,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
         dfree(ctx->d_picinst);
         dfree(ctx->d_dep);
         dfree(ctx->d_dep_tiles);
+        dfree(ctx->d_limits);
         delete ctx;
         return MUCITE_E_OOM;
     }
@@ -710,6 +754,7 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_dep);
     dfree(ctx->d_dep_tiles);
     dfree(ctx->d_rf);
+    dfree(ctx->d_limits);
     drop_graph(ctx);
     delete ctx;
 }
@@ -839,6 +884,19 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
         CK(cudaMemcpy(ctx->d_a, a.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_c, c.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_A, A.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
+        // metal flag of each PIC node: the electrode mask at the nearest static node
+        std::vector<uint8_t> pm((size_t)pic->nr * pic->nz);
+        const double sdr = g->R / (g->nr - 1), sdz = (g->z1 - g->z0) / (g->nz - 1);
+        for (int j = 0; j < pic->nz; ++j)
+            for (int i = 0; i < pic->nr; ++i) {
+                int si = (int)std::lrint(i * G.dr / sdr), sj = (int)std::lrint(j * G.dz / sdz);
+                si = std::min(std::max(si, 0), g->nr - 1);
+                sj = std::min(std::max(sj, 0), g->nz - 1);
+                pm[(size_t)j * pic->nr + i] = metal_mask[(size_t)sj * g->nr + si] ? 1 : 0;
+                ctx->pic_has_metal = ctx->pic_has_metal || pm[(size_t)j * pic->nr + i];
+            }
+        CK(cudaMalloc(&ctx->d_pic_metal, pm.size()));
+        CK(cudaMemcpy(ctx->d_pic_metal, pm.data(), pm.size(), cudaMemcpyHostToDevice));
         G.S = ctx->d_S;
         G.cp = ctx->d_cp;
         G.invm = ctx->d_invm;
@@ -917,12 +975,20 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
         CK(cudaMalloc(&I.pic.hat, nu * sizeof(float)));
         CK(cudaMalloc(&I.pic.d32, nu * sizeof(float)));
         CK(cudaMalloc(&I.pic.esc, nn * sizeof(float2)));
-        CK(cudaMalloc(&I.pic.red, 4 * sizeof(double)));
+        CK(cudaMalloc(&I.pic.red, 8 * sizeof(double)));
         CK(cudaMalloc(&I.pic.conv, sizeof(int)));
         CK(cudaMemsetAsync(I.pic.phi, 0, nn * sizeof(double), ctx->stream));
         CK(cudaMemsetAsync(I.pic.esc, 0, nn * sizeof(float2), ctx->stream));
         CK(cudaMemsetAsync(I.pic.Q, 0, nn * sizeof(unsigned long long), ctx->stream));
-        CK(cudaMemsetAsync(I.pic.red, 0, 4 * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(I.pic.red, 0, 8 * sizeof(double), ctx->stream));
+        I.pic_masked = run->pic_masked != 0 && ctx->pic_has_metal;
+        if (I.pic_masked) {
+            CK(cudaMalloc(&I.pic.r64, nu * sizeof(double)));
+            CK(cudaMalloc(&I.pic.z64, nu * sizeof(double)));
+            CK(cudaMalloc(&I.pic.q64, nu * sizeof(double)));
+            CK(cudaMalloc(&I.pic.p64, nn * sizeof(double)));
+            CK(cudaMemsetAsync(I.pic.p64, 0, nn * sizeof(double), ctx->stream));
+        }
         if (run->precision == MUCITE_FP64) {
             CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));
             CK(cudaMalloc(&I.pic.ez64, nn * sizeof(double)));
@@ -1147,13 +1213,80 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
 mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block)
 {
     if (!ctx) return MUCITE_E_ARG;
-    if (steps_per_launch < 0 || steps_per_launch > 12000)
-        return fail(ctx, MUCITE_E_ARG, "steps_per_launch must be in [1, 12000]");
+    if (steps_per_launch < 0 || steps_per_launch > 6000)
+        return fail(ctx, MUCITE_E_ARG, "steps_per_launch must be in [1, 6000]");
     if (threads_per_block < 0 || threads_per_block % 32 != 0 || threads_per_block > 256)
         return fail(ctx, MUCITE_E_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
     drop_graph(ctx);
     if (steps_per_launch) ctx->steps_per_launch = steps_per_launch;
     if (threads_per_block) ctx->threads = threads_per_block;
+    return MUCITE_OK;
+}
+
+mucite_status mucite_set_dt(mucite_ctx *ctx, int instance, double dt)
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    if (!(dt > 0.0)) return fail(ctx, MUCITE_E_ARG, "dt must be > 0");
+    Instance &I = ctx->inst[instance];
+    DevGuard dg(ctx->device);
+    drop_graph(ctx);
+    if (I.run.f_rf != 0.0) {
+        const double x = I.rf_phase0 + (double)(I.step - I.seg_step0) * (I.run.dt * I.run.f_rf);
+        I.rf_phase0 = x - floor(x);
+    }
+    I.seg_step0 = I.step;
+    I.run.dt = dt;
+    bind_params(ctx, I);
+    return MUCITE_OK;
+}
+
+mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6])
+{
+    const mucite_status st = check_instance(ctx, instance);
+    if (st != MUCITE_OK) return st;
+    if (!out) return fail(ctx, MUCITE_E_ARG, "out is NULL");
+    Instance &I = ctx->inst[instance];
+    DevGuard dg(ctx->device);
+    unsigned *d_out = ctx->d_limits;
+    const unsigned init[3] = {0u, 0u, 0x7f800000u};
+    CK(cudaMemcpyAsync(d_out, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+    LimitArgs A{};
+    A.precision = I.run.precision;
+    A.x = (char *)I.pool + I.lay.off_x;
+    A.y = (char *)I.pool + I.lay.off_y;
+    A.z = (char *)I.pool + I.lay.off_z;
+    A.vx = (char *)I.pool + I.lay.off_vx;
+    A.vy = (char *)I.pool + I.lay.off_vy;
+    A.vz = (char *)I.pool + I.lay.off_vz;
+    A.status = at<uint8_t>(I.pool, I.lay.off_status);
+    A.n = I.n_slots;
+    A.sx_inv = kLat / ctx->g.R;
+    A.sz_inv = kLat / (ctx->g.z1 - ctx->g.z0);
+    A.gz0 = ctx->g.z0;
+    A.srf = rf_scalar(I, I.step);
+    const double M = I.ion.mass_da * kDa;
+    A.kick_m = (float)(I.ion.charge * kE / M);
+    A.kT_over_M_coef = (float)(kKB / M);
+    A.out = d_out;
+    launch_dt_limits(grid_f32(ctx), I.f32, A, ctx->stream);
+    ctx->launches++;
+    CKL();
+    unsigned h[3];
+    CK(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float lam, vmax, acc;
+    memcpy(&lam, &h[0], 4);
+    memcpy(&vmax, &h[1], 4);
+    memcpy(&acc, &h[2], 4);
+    const double dr = ctx->g.R / (ctx->g.nr - 1), dz = (ctx->g.z1 - ctx->g.z0) / (ctx->g.nz - 1);
+    out[0] = (I.run.f_rf > 0.0 && I.run.v_rf != 0.0) ? 0.05 / I.run.f_rf : INFINITY;
+    out[1] = lam > 0.0f ? 0.1 / lam : INFINITY;
+    out[2] = acc;
+    out[3] = vmax > 0.0f ? 0.5 * std::min(dr, dz) / vmax : INFINITY;
+    out[4] = I.run.langevin ? 2e-9 : INFINITY;
+    out[5] = out[0];
+    for (int k = 1; k < 5; ++k) out[5] = std::min(out[5], out[k]);
     return MUCITE_OK;
 }
 

@@ -89,8 +89,11 @@ struct InstF32 {
     int32_t *t_term;
     int64_t n_slots;
     int64_t step0;
-    double v_rf, dtf, phi_rf;  // RF scalar V * cos(2 pi frac(n dt f) + phi), FP64
-    float *rf;                 // RF scalars of the current launch, one per micro step
+    double v_rf, dtf, phi_rf;  // RF scalar V cos(2 pi frac(phase0 + (n - seg0) dt f) + phi), FP64
+    double rf_phase0;          // RF phase (cycles) at the start of the current dt segment
+    int64_t seg_step0;         // step count at the start of the current dt segment
+    float *rf;                 // RF scalars of the launch at half-step spacing: [2k] step k, [2k+1] k + 1/2
+    int rk4;                   // RK4 pusher instead of the leapfrog
     float kick;                // q e dt / m
     float dc_scale;
     float cxs, czs;            // dt * 2^30 / R, dt * 2^30 / (z1 - z0): velocity -> lattice step
@@ -131,6 +134,7 @@ struct InstF64 {
     int langevin;
     double lv_z0, lv_z1, lv_switch;
     double q_abs;              // |q| e
+    int rk4;
     uint64_t seed;
     int64_t zexit_q, rdet_q;
     float hit;

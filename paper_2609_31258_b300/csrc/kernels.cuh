@@ -42,6 +42,21 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
                      cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
 int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras);
-void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, cudaStream_t s);
+void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, double srf_half,
+                     double srf_next, cudaStream_t s);
+// Eq. 1 limits of one instance: out (device) [0] max rate, [1] max |v|,
+// [2] min max(|v|, v_th)/|a|, as float bit patterns reduced with integer atomics.
+struct LimitArgs {
+    int precision;
+    const void *x, *y, *z, *vx, *vy, *vz;
+    const uint8_t *status;
+    int64_t n;
+    double sx_inv, sz_inv, gz0;   // lattice -> metres for the FP32 pool
+    double srf;
+    float kick_m;                 // q/M (acceleration per V/m)
+    float kT_over_M_coef;         // k_B / M
+    unsigned *out;
+};
+void launch_dt_limits(const GridF32 &G, const InstF32 &P, const LimitArgs &A, cudaStream_t s);
 
 } // namespace mucite

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) pic_prepare_kernel(PicGeom G, const PicIn
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
         I.Q[e] = 0ull;
-    if (blockIdx.x == 0 && threadIdx.x < 4) I.red[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 8) I.red[threadIdx.x] = 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
 }
 
@@ -312,14 +312,8 @@ void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int 
     deposit_kernel<<<total_tiles, 256, 0, s>>>(d_args, d_tile_start, n_inst);
 }
 
-int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
-                     cudaStream_t s)
+int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
-    int launches = 0;
-    const int64_t nu = (int64_t)G.M * G.Nu;
-    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
-    bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    ++launches;
     DstGemm fwd{}, inv{};
     // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
     fwd.S = G.S; fwd.a_is_S = 0; fwd.a_sel = 0; fwd.b_is_S = 1; fwd.c_sel = 1;
@@ -333,20 +327,36 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
     inv.alpha = 1.0f;
     const dim3 gf((G.M + 63) / 64, (G.Nu + 63) / 64, n_inst);
     const dim3 gi((G.Nu + 63) / 64, (G.M + 63) / 64, n_inst);
+    dst_gemm_kernel<true, true><<<gf, 256, 0, s>>>(fwd, d_insts);
+    thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    dst_gemm_kernel<false, false><<<gi, 256, 0, s>>>(inv, d_insts);
+    return 3;
+}
+
+void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+{
+    const int64_t nn = (int64_t)G.pnr * G.pnz;
+    esc_kernel<<<dim3((unsigned)std::min<int64_t>((nn + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(G, d_insts);
+}
+
+int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
+                     cudaStream_t s)
+{
+    int launches = 0;
+    const int64_t nu = (int64_t)G.M * G.Nu;
+    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
+    bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    ++launches;
     for (int it = 0; it <= max_refine; ++it) {
         residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
         check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);
         launches += 2;
         if (it == max_refine) break;
-        dst_gemm_kernel<true, true><<<gf, 256, 0, s>>>(fwd, d_insts);
-        thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        dst_gemm_kernel<false, false><<<gi, 256, 0, s>>>(inv, d_insts);
+        launches += launch_fast_solve(G, d_insts, n_inst, s);
         update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        launches += 4;
+        launches += 1;
     }
-    const int64_t nn = (int64_t)G.pnr * G.pnz;
-    esc_kernel<<<dim3((unsigned)std::min<int64_t>((nn + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(
-        G, d_insts);
+    launch_esc(G, d_insts, n_inst, s);
     return launches + 1;
 }
 

@@ -17,6 +17,7 @@ struct PicGeom {
     const float *invm;       // [Nu][M] 1 / m_i(k)
     const float *lo;         // [Nu] a_i (sub-diagonal)
     const double *a, *c, *A; // [Nu] FP64 operator coefficients
+    const uint8_t *metal;    // [pnz][pnr] metal nodes (mask-aware solve) or NULL
 };
 
 // Per-instance buffers of the space-charge solve.
@@ -28,8 +29,10 @@ struct PicInst {
     float *d32;              // [M][Nu] correction
     float2 *esc;             // [pnz][pnr] (E_r, E_z)
     double *er64, *ez64;     // FP64 copies for the FP64 path (or NULL)
-    double *red;             // [0] ||b||^2, [1] ||r||^2, [2] rel. residual, [3] refinements
+    double *red;             // [0] ||b||^2, [1] ||r||^2, [2] rel. residual, [3] iterations, [4..6] PCG scalars
     int *conv;               // converged flag
+    double *r64, *z64, *q64; // [M][Nu] PCG vectors (mask-aware solve) or NULL
+    double *p64;             // [pnz][pnr] PCG search direction or NULL
 };
 
 struct DepositArgs {
@@ -59,5 +62,12 @@ void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cu
 // Returns the number of kernel launches issued.
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
                      cudaStream_t s);
+// Maskless fast solve A d = r: r32 -> (DST-I, Thomas per mode, inverse DST-I) -> d32.
+int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
+// Mask-aware solve by PCG preconditioned with the fast solve (pic_masked.cu).
+int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_iter, double tol,
+                            cudaStream_t s);
+// E_SCE by central differences of Phi.
+void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 
 } // namespace mucite

@@ -1,0 +1,216 @@
+// Mask-aware space-charge solve ("Zero perturbation potential is imposed at
+// the axial boundaries, the outer radial boundary, and metal mask nodes").
+//
+// A direct DST/tridiagonal solve cannot impose Phi = 0 at interior metal
+// nodes, so the masked system A_m Phi = b_m (metal rows replaced by the
+// identity, metal columns removed, b = 0 at metal) is solved by
+// preconditioned conjugate gradients in FP64, with the maskless fast solver
+// of pic.cu (FP32 DST-I + per-mode Thomas + inverse DST-I) as preconditioner,
+// restricted to the fluid nodes: z = P A^-1 P r. A_m and A are both negative
+// definite, so the usual PCG recurrences apply unchanged. Scalars (alpha,
+// beta, convergence) live on the device; iterations stop at
+// ||b - A_m Phi|| / ||b|| <= tol without a host round trip.
+// blockIdx.z selects the instance.
+#include "common.cuh"
+#include "pic.cuh"
+
+namespace mucite {
+
+namespace {
+
+// red slots of a masked solve
+enum { kBB = 0, kRR = 1, kREL = 2, kIT = 3, kRZ = 4, kRZN = 5, kPQ = 6 };
+
+__device__ __forceinline__ double block_sum_m(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// (A x)_ij on an unknown node for a full-grid vector x (zero on the Dirichlet
+// boundary and, for the vectors used here, on metal nodes).
+__device__ __forceinline__ double apply_A(const PicGeom &G, const double *x, int i, int j)
+{
+    const double *ph = x + (size_t)j * G.pnr + i;
+    const double c = ph[0];
+    const double w = i > 0 ? ph[-1] : 0.0;
+    return G.a[i] * w + G.c[i] * ph[1] - (G.a[i] + G.c[i]) * c + G.A[i] * (ph[G.pnr] - 2.0 * c + ph[-G.pnr]);
+}
+
+__device__ __forceinline__ bool is_metal(const PicGeom &G, int i, int j)
+{
+    return G.metal[(size_t)j * G.pnr + i] != 0;
+}
+
+} // namespace
+
+// r = b_m - A_m Phi on the unknowns (FP64 and FP32 copies), ||b_m||^2.
+__global__ void __launch_bounds__(256) pcg_init_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double bb = 0.0, rr = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        double r = 0.0;
+        if (!is_metal(G, i, j)) {
+            const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
+            r = b - apply_A(G, I.phi, i, j);
+            bb += b * b;
+        }
+        I.r64[e] = r;
+        I.r32[e] = (float)r;
+        rr += r * r;
+    }
+    bb = block_sum_m(bb, sh);
+    __syncthreads();
+    rr = block_sum_m(rr, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&I.red[kBB], bb);
+        atomicAdd(&I.red[kRR], rr);
+    }
+}
+
+// z = P A^-1 P r from the fast solve's output d32; rz = r . z.
+__global__ void __launch_bounds__(256) pcg_z_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double rz = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        const double z = is_metal(G, i, j) ? 0.0 : (double)I.d32[e];
+        I.z64[e] = z;
+        rz += I.r64[e] * z;
+    }
+    rz = block_sum_m(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&I.red[kRZN], rz);
+}
+
+// beta = rz_new / rz (0 on the first iteration), p = z + beta p (full grid).
+__global__ void __launch_bounds__(256) pcg_p_kernel(PicGeom G, const PicInst *insts, int first)
+{
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const double beta = first ? 0.0 : I.red[kRZN] / I.red[kRZ];
+    const int64_t n = (int64_t)G.M * G.Nu;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        double *p = I.p64 + (size_t)j * G.pnr + i;
+        *p = I.z64[e] + beta * *p;
+    }
+}
+
+// q = A_m p, pq = p . q.
+__global__ void __launch_bounds__(256) pcg_q_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double pq = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        const double q = is_metal(G, i, j) ? 0.0 : apply_A(G, I.p64, i, j);
+        I.q64[e] = q;
+        pq += I.p64[(size_t)j * G.pnr + i] * q;
+    }
+    pq = block_sum_m(pq, sh);
+    if (threadIdx.x == 0) atomicAdd(&I.red[kPQ], pq);
+}
+
+// alpha = rz / pq; Phi += alpha p; r -= alpha q; ||r||^2.
+__global__ void __launch_bounds__(256) pcg_xr_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const double alpha = I.red[kRZ] / I.red[kPQ];
+    const int64_t n = (int64_t)G.M * G.Nu;
+    double rr = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
+        const size_t f = (size_t)j * G.pnr + i;
+        I.phi[f] += alpha * I.p64[f];
+        const double r = I.r64[e] - alpha * I.q64[e];
+        I.r64[e] = r;
+        I.r32[e] = (float)r;
+        rr += r * r;
+    }
+    rr = block_sum_m(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&I.red[kRR], rr);
+}
+
+// One thread per instance: rel = ||r|| / ||b|| after the initial residual
+// (phase 0) or after an update (phase 2, also counts the iteration); the
+// solve is converged when rel <= tol.
+__global__ void pcg_scalar_kernel(const PicInst *insts, double tol, int phase)
+{
+    const PicInst &I = insts[blockIdx.x];
+    if (threadIdx.x != 0 || *I.conv) return;
+    double *red = I.red;
+    const double rel = red[kBB] > 0.0 ? sqrt(red[kRR] / red[kBB]) : 0.0;
+    red[kREL] = rel;
+    red[kRR] = 0.0;
+    if (phase == 2) red[kIT] += 1.0;
+    if (rel <= tol) *I.conv = 1;
+}
+
+// After p = z + beta p: rz <- rz_new, clear the accumulators of the next round.
+__global__ void pcg_rotate_kernel(const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.x];
+    if (threadIdx.x != 0 || *I.conv) return;
+    I.red[kRZ] = I.red[kRZN];
+    I.red[kRZN] = 0.0;
+    I.red[kPQ] = 0.0;
+}
+
+int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_iter, double tol,
+                            cudaStream_t s)
+{
+    int launches = 0;
+    const int64_t nu = (int64_t)G.M * G.Nu;
+    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
+    const dim3 gv(blocks, 1, n_inst);
+    pcg_init_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+    pcg_scalar_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol, 0);
+    launches += 2;
+    // z0 = P A^-1 P r0, p0 = z0
+    launches += launch_fast_solve(G, d_insts, n_inst, s);
+    pcg_z_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+    pcg_p_kernel<<<gv, 256, 0, s>>>(G, d_insts, 1);
+    pcg_rotate_kernel<<<n_inst, 32, 0, s>>>(d_insts);
+    launches += 3;
+    for (int it = 0; it < max_iter; ++it) {
+        pcg_q_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+        pcg_xr_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+        pcg_scalar_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol, 2);
+        launches += 3;
+        if (it == max_iter - 1) break;
+        launches += launch_fast_solve(G, d_insts, n_inst, s);
+        pcg_z_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+        pcg_p_kernel<<<gv, 256, 0, s>>>(G, d_insts, 0);
+        pcg_rotate_kernel<<<n_inst, 32, 0, s>>>(d_insts);
+        launches += 3;
+    }
+    return launches;
+}
+
+} // namespace mucite

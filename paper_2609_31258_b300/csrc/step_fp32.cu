@@ -162,11 +162,29 @@ __device__ __forceinline__ float teff_of(const InstF32 &P, float eint)
     return P.tcap + (e - P.ecap);
 }
 
-// Collisions of one pack during one step of length dt. Returns accepted
-// events; sets *ovf when the candidate cap was reached.
+// Philox blocks of one candidate beyond the first: B (partner), C
+// (scattering and exchange) and the next candidate's A are independent, so
+// they are drawn together and their ten-round chains interleave.
+struct Blocks3 {
+    uint4 B, C, A;
+};
+
+__device__ __forceinline__ Blocks3 draw_bca(uint32_t pack, uint32_t step, uint32_t k, uint32_t k0,
+                                            uint32_t k1)
+{
+    Blocks3 r;
+    r.B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), k0, k1);
+    r.C = philox10(make_uint4(pack, step, 3u * k + 2u, 0u), k0, k1);
+    r.A = philox10(make_uint4(pack, step, 3u * k + 3u, 0u), k0, k1);
+    return r;
+}
+
+// Collisions of one pack during one step of length dt, given the step's first
+// draw block A (block 0). Returns accepted events; sets *ovf when the
+// candidate cap was reached.
 __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_t pack,
-                                       uint32_t step, float &vx, float &vy, float &vz, float &eint,
-                                       int &ovf)
+                                       uint32_t step, uint4 A, float &vx, float &vy, float &vz,
+                                       float &eint, int &ovf)
 {
     ovf = 0;
     if (!(L.nsig > 0.0f) || !(L.T > 0.0f)) return 0;
@@ -177,10 +195,10 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
     for (int k = 0; k < kKmax; ++k) {
         const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
         const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
-        const uint4 A = philox10(make_uint4(pack, step, 3u * k, 0u), P.key0, P.key1);
         t += __fdividef(-__logf(u01f(A.x)), L.nsig * (w + cbar));
         if (t >= P.dt) return acc;
-        const uint4 B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), P.key0, P.key1);
+        const Blocks3 D = draw_bca(pack, step, (uint32_t)k, P.key0, P.key1);
+        const uint4 B = D.B, Cc = D.C;
         // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
         // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
         // N^2/2 = -ln(u) cos^2(2 pi u'). One branch-free path for both laws.
@@ -205,9 +223,10 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
         const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
         const float g2 = gx * gx + gy * gy + gz * gz;
         const float g = sqrt_fast(g2);
-        if (!(u01f(A.z) * (w + cmag) < g)) continue;
+        const bool accept = u01f(A.z) * (w + cmag) < g;
+        A = D.A;
+        if (!accept) continue;
         ++acc;
-        const uint4 Cc = philox10(make_uint4(pack, step, 3u * k + 2u, 0u), P.key0, P.key1);
         const float Vx = P.fM * vx + P.fm * (L.ux + cx);
         const float Vy = P.fM * vy + P.fm * (L.uy + cy);
         const float Vz = P.fM * vz + P.fm * (L.uz + cz);
@@ -302,6 +321,24 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
     return __reduce_add_sync(0xffffffffu, v);
 }
 
+// Velocity increment kick * E_tot over one step at the RK4 stage position
+// x + h v (h v given in m/s times the step, i.e. the stage's fraction of
+// the step times the stage velocity), with RF scalar srf.
+__device__ __forceinline__ void stage_kick(const GridF32 &G, const InstF32 &P, int32_t xq, int32_t yq,
+                                           int32_t zq, float hvx, float hvy, float hvz, float srf, float &kx,
+                                           float &ky, float &kz)
+{
+    const int32_t sx = xq + __float2int_rn(fminf(fmaxf(hvx * P.cxs, -1.0e9f), 1.0e9f));
+    const int32_t sy = yq + __float2int_rn(fminf(fmaxf(hvy * P.cxs, -1.0e9f), 1.0e9f));
+    const int32_t sz = zq + __float2int_rn(fminf(fmaxf(hvz * P.czs, -1.0e9f), 1.0e9f));
+    const float fx = (float)sx, fy = (float)sy;
+    Local L;
+    gather(G, P, fx, fy, lattice_r(fx, fy), sz, L);
+    kx = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
+    ky = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
+    kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+}
+
 // Advance the `blockDim.x` packs of one tile of instance P starting at pack
 // `off` by `nsteps` micro steps, and add the warp totals to the counters.
 template <bool kCollide, bool kExtras>
@@ -320,6 +357,10 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
         int st = MUCITE_ACTIVE;
         int k = 0;
         const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
+        // first draw block of the coming step, drawn one step ahead so that its
+        // chain overlaps the kick, drift and classification of the step before
+        uint4 A0 = kCollide ? philox10(make_uint4(pack, (uint32_t)P.step0, 0u, 0u), P.key0, P.key1)
+                            : make_uint4(0u, 0u, 0u, 0u);
         for (; k < nsteps; ++k) {
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
@@ -332,11 +373,12 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
                     langevin_step(P, L, pack, n, vx, vy, vz);
                 } else {
                     int ovf;
-                    n_coll += collide(P, L, pack, n, vx, vy, vz, eint, ovf);
+                    n_coll += collide(P, L, pack, n, A0, vx, vy, vz, eint, ovf);
                     n_ovf += ovf;
                 }
+                A0 = philox10(make_uint4(pack, n + 1u, 0u, 0u), P.key0, P.key1);
             }
-            const float srf = s_rf[k];
+            const float srf = s_rf[2 * k];
             const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
             if (kExtras && P.tst && !lv) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
@@ -344,12 +386,38 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
                 lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
             }
-            vx = add_sr(vx, P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx), dither(h1, 0));
-            vy = add_sr(vy, P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy), dither(h1, 11));
-            vz = add_sr(vz, P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz), dither(h1, 22));
-            xq += lattice_step(vx * P.cxs, dither(h2, 0));
-            yq += lattice_step(vy * P.cxs, dither(h2, 11));
-            zq += lattice_step(vz * P.czs, dither(h2, 22));
+            if (kExtras && P.rk4) {
+                // RK4 under the instantaneous field: stages at t, t + dt/2 (x2)
+                // and t + dt; stage positions rounded to the lattice
+                const float sh = s_rf[2 * k + 1], s1 = s_rf[2 * k + 2];
+                const float k1x = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
+                const float k1y = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
+                const float k1z = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+                float k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+                stage_kick(G, P, xq, yq, zq, 0.5f * vx, 0.5f * vy, 0.5f * vz, sh, k2x, k2y, k2z);
+                const float v2x = vx + 0.5f * k1x, v2y = vy + 0.5f * k1y, v2z = vz + 0.5f * k1z;
+                stage_kick(G, P, xq, yq, zq, 0.5f * v2x, 0.5f * v2y, 0.5f * v2z, sh, k3x, k3y, k3z);
+                const float v3x = vx + 0.5f * k2x, v3y = vy + 0.5f * k2y, v3z = vz + 0.5f * k2z;
+                stage_kick(G, P, xq, yq, zq, v3x, v3y, v3z, s1, k4x, k4y, k4z);
+                const float v4x = vx + k3x, v4y = vy + k3y, v4z = vz + k3z;
+                const float c6 = 1.0f / 6.0f;
+                const float ux = (vx + 2.0f * v2x + 2.0f * v3x + v4x) * c6;
+                const float uy = (vy + 2.0f * v2y + 2.0f * v3y + v4y) * c6;
+                const float uz = (vz + 2.0f * v2z + 2.0f * v3z + v4z) * c6;
+                vx = add_sr(vx, (k1x + 2.0f * k2x + 2.0f * k3x + k4x) * c6, dither(h1, 0));
+                vy = add_sr(vy, (k1y + 2.0f * k2y + 2.0f * k3y + k4y) * c6, dither(h1, 11));
+                vz = add_sr(vz, (k1z + 2.0f * k2z + 2.0f * k3z + k4z) * c6, dither(h1, 22));
+                xq += lattice_step(ux * P.cxs, dither(h2, 0));
+                yq += lattice_step(uy * P.cxs, dither(h2, 11));
+                zq += lattice_step(uz * P.czs, dither(h2, 22));
+            } else {
+                vx = add_sr(vx, P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx), dither(h1, 0));
+                vy = add_sr(vy, P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy), dither(h1, 11));
+                vz = add_sr(vz, P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz), dither(h1, 22));
+                xq += lattice_step(vx * P.cxs, dither(h2, 0));
+                yq += lattice_step(vy * P.cxs, dither(h2, 11));
+                zq += lattice_step(vz * P.czs, dither(h2, 22));
+            }
             fx = (float)xq;
             fy = (float)yq;
             rr = lattice_r(fx, fy);
@@ -409,7 +477,7 @@ __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF
             for (int w = threadIdx.x; w < (int)(sizeof(InstF32) / 4); w += blockDim.x)
                 reinterpret_cast<uint32_t *>(p_raw)[w] = src[w];
             __syncthreads();
-            for (int k = threadIdx.x; k < nsteps; k += blockDim.x) s_rf[k] = P.rf[k];
+            for (int k = threadIdx.x; k <= 2 * nsteps; k += blockDim.x) s_rf[k] = P.rf[k];
             __syncthreads();
             cur = lo;
         }
@@ -417,18 +485,19 @@ __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF
     }
 }
 
-// RF scalar of Eq. 4 for the next `nsteps` steps of every instance: the
-// phase frac(n dt f) is taken in FP64 from the integer step count.
+// RF scalars of Eq. 4 for the next `nsteps` steps of every instance at
+// half-step spacing (entry j is time step0 + j/2): the phase
+// frac(phase0 + (n - seg0) dt f) is taken in FP64 from the integer step count.
 __global__ void rf_table_kernel(const InstF32 *insts, int nsteps)
 {
     const InstF32 &P = insts[blockIdx.x];
-    for (int k = threadIdx.x; k < nsteps; k += blockDim.x) {
+    for (int j = threadIdx.x; j <= 2 * nsteps; j += blockDim.x) {
         float v = 0.0f;
         if (P.v_rf != 0.0 && P.dtf != 0.0) {
-            const double x = (double)(P.step0 + k) * P.dtf;
+            const double x = P.rf_phase0 + ((double)(P.step0 - P.seg_step0) + 0.5 * j) * P.dtf;
             v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
         }
-        P.rf[k] = v;
+        P.rf[j] = v;
     }
 }
 
@@ -446,7 +515,7 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
                      cudaStream_t s)
 {
     rf_table_kernel<<<n_inst, 128, 0, s>>>(d_insts, nsteps);
-    const size_t smem = sizeof(float) * (size_t)nsteps;
+    const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
     if (collide && extras)
         step_f32_kernel<true, true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
     else if (collide)
@@ -465,7 +534,7 @@ void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t
 int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras)
 {
     int b = 0;
-    const size_t smem = sizeof(float) * (size_t)nsteps;
+    const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
     if (collide && extras)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, true>, threads, smem);
     else if (collide)
@@ -475,6 +544,79 @@ int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras)
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false>, threads, smem);
     return b;
+}
+
+} // namespace mucite
+
+namespace mucite {
+
+namespace {
+
+__device__ __forceinline__ int32_t q32l(double v)
+{
+    const double r = rint(v);
+    if (r < -2147483648.0) return INT32_MIN;
+    if (r > 2147483647.0) return INT32_MAX;
+    return (int32_t)r;
+}
+
+} // namespace
+
+// Per-pack quantities of the Eq. 1 limits, reduced over the active packs:
+// largest expected collision rate, largest speed, smallest
+// 0.1 max(|v|, v_th) / |a| (positive floats ordered as unsigned integers).
+__global__ void __launch_bounds__(256) dt_limits_kernel(GridF32 G, InstF32 P, LimitArgs A)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lam = 0.0f, vmax = 0.0f, acc = __int_as_float(0x7f800000);
+    if (p < A.n && A.status[p] == MUCITE_ACTIVE) {
+        int32_t xq, yq, zq;
+        float vx, vy, vz;
+        if (A.precision == MUCITE_FP32) {
+            xq = ((const int32_t *)A.x)[p];
+            yq = ((const int32_t *)A.y)[p];
+            zq = ((const int32_t *)A.z)[p];
+            vx = ((const float *)A.vx)[p];
+            vy = ((const float *)A.vy)[p];
+            vz = ((const float *)A.vz)[p];
+        } else {
+            xq = q32l(((const double *)A.x)[p] * A.sx_inv);
+            yq = q32l(((const double *)A.y)[p] * A.sx_inv);
+            zq = q32l((((const double *)A.z)[p] - A.gz0) * A.sz_inv);
+            vx = (float)((const double *)A.vx)[p];
+            vy = (float)((const double *)A.vy)[p];
+            vz = (float)((const double *)A.vz)[p];
+        }
+        const float fx = (float)xq, fy = (float)yq;
+        Local L;
+        gather(G, P, fx, fy, lattice_r(fx, fy), zq, L);
+        if (L.nsig > 0.0f && L.T > 0.0f) lam = collision_rate(P, L, vx, vy, vz);
+        vmax = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float srf = (float)A.srf;
+        const float ax = A.kick_m * (P.dc_scale * L.edx + srf * L.erx + L.esx);
+        const float ay = A.kick_m * (P.dc_scale * L.edy + srf * L.ery + L.esy);
+        const float az = A.kick_m * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+        const float am = sqrtf(ax * ax + ay * ay + az * az);
+        const float vth = L.T > 0.0f ? sqrtf(A.kT_over_M_coef * L.T) : 0.0f;
+        if (am > 0.0f) acc = 0.1f * fmaxf(vmax, vth) / am;
+    }
+    unsigned ul = __float_as_uint(lam), uv = __float_as_uint(vmax), ua = __float_as_uint(acc);
+    for (int o = 16; o > 0; o >>= 1) {
+        ul = max(ul, __shfl_down_sync(0xffffffffu, ul, o));
+        uv = max(uv, __shfl_down_sync(0xffffffffu, uv, o));
+        ua = min(ua, __shfl_down_sync(0xffffffffu, ua, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&A.out[0], ul);
+        atomicMax(&A.out[1], uv);
+        atomicMin(&A.out[2], ua);
+    }
+}
+
+void launch_dt_limits(const GridF32 &G, const InstF32 &P, const LimitArgs &A, cudaStream_t s)
+{
+    if (A.n <= 0) return;
+    dt_limits_kernel<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(G, P, A);
 }
 
 } // namespace mucite

@@ -208,8 +208,17 @@ __device__ int classify_d(const GridF64 &G, const InstF64 &P, double x, double y
 
 } // namespace
 
+// (q/m) E_tot at a position for a given RF scalar (Eq. 3, Eq. 4).
+__device__ void accel_d(const GridF64 &G, const InstF64 &P, double x, double y, double z, double srf,
+                        double a[3])
+{
+    LocalD L;
+    gather_d(G, P, x, y, z, L);
+    for (int d = 0; d < 3; ++d) a[d] = P.qm * (P.dc_scale * L.ed[d] + srf * L.er[d] + L.es[d]);
+}
+
 __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int64_t step,
-                                                       double srf)
+                                                       double srf, double srf_half, double srf_next)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned done = 0, coll = 0, ovf_n = 0;
@@ -231,11 +240,28 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
             const double Te = teff_d(P.prof, eint);
             lnsy -= P.tst_a * Te * exp(-P.tst_b / Te) * P.dt;
         }
-        for (int d = 0; d < 3; ++d)
-            v[d] += P.qm * (P.dc_scale * L.ed[d] + srf * L.er[d] + L.es[d]) * P.dt;
-        x += v[0] * P.dt;
-        y += v[1] * P.dt;
-        z += v[2] * P.dt;
+        if (P.rk4) {
+            // RK4 under the instantaneous field: t, t + dt/2 (twice), t + dt
+            const double h = P.dt;
+            double a1[3], a2[3], a3[3], a4[3], v2[3], v3[3], v4[3];
+            for (int d = 0; d < 3; ++d) a1[d] = P.qm * (P.dc_scale * L.ed[d] + srf * L.er[d] + L.es[d]);
+            for (int d = 0; d < 3; ++d) v2[d] = v[d] + 0.5 * h * a1[d];
+            accel_d(G, P, x + 0.5 * h * v[0], y + 0.5 * h * v[1], z + 0.5 * h * v[2], srf_half, a2);
+            for (int d = 0; d < 3; ++d) v3[d] = v[d] + 0.5 * h * a2[d];
+            accel_d(G, P, x + 0.5 * h * v2[0], y + 0.5 * h * v2[1], z + 0.5 * h * v2[2], srf_half, a3);
+            for (int d = 0; d < 3; ++d) v4[d] = v[d] + h * a3[d];
+            accel_d(G, P, x + h * v3[0], y + h * v3[1], z + h * v3[2], srf_next, a4);
+            x += h / 6.0 * (v[0] + 2.0 * v2[0] + 2.0 * v3[0] + v4[0]);
+            y += h / 6.0 * (v[1] + 2.0 * v2[1] + 2.0 * v3[1] + v4[1]);
+            z += h / 6.0 * (v[2] + 2.0 * v2[2] + 2.0 * v3[2] + v4[2]);
+            for (int d = 0; d < 3; ++d) v[d] += h / 6.0 * (a1[d] + 2.0 * a2[d] + 2.0 * a3[d] + a4[d]);
+        } else {
+            for (int d = 0; d < 3; ++d)
+                v[d] += P.qm * (P.dc_scale * L.ed[d] + srf * L.er[d] + L.es[d]) * P.dt;
+            x += v[0] * P.dt;
+            y += v[1] * P.dt;
+            z += v[2] * P.dt;
+        }
         const int st = classify_d(G, P, x, y, z);
         P.x[p] = x; P.y[p] = y; P.z[p] = z;
         P.vx[p] = v[0]; P.vy[p] = v[1]; P.vz[p] = v[2];
@@ -257,12 +283,13 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
     }
 }
 
-void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, cudaStream_t s)
+void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, double srf_half,
+                     double srf_next, cudaStream_t s)
 {
     if (P.n_slots <= 0) return;
     const int threads = 256;
     const int64_t blocks = (P.n_slots + threads - 1) / threads;
-    step_f64_kernel<<<(unsigned)blocks, threads, 0, s>>>(G, P, step, srf);
+    step_f64_kernel<<<(unsigned)blocks, threads, 0, s>>>(G, P, step, srf, srf_half, srf_next);
 }
 
 } // namespace mucite

@@ -23,7 +23,8 @@ MAX_INSTANCES = 256
 EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_fields",
            "mucite_state_layout", "mucite_inject", "mucite_release", "mucite_resume", "mucite_step",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
-           "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc"]
+           "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
+           "mucite_dt_limits"]
 
 
 class MuciteError(RuntimeError):
@@ -58,7 +59,8 @@ class Run(C.Structure):
                 ("exit_bin_steps", C.c_int32), ("n_exit_bins", C.c_int32), ("n_r_bins", C.c_int32),
                 ("n_ke_bins", C.c_int32), ("n_teff_bins", C.c_int32), ("n_loss_r", C.c_int32),
                 ("n_loss_z", C.c_int32), ("ke_max_ev", C.c_double), ("teff_max", C.c_double),
-                ("langevin", C.c_int32), ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double)]
+                ("langevin", C.c_int32), ("lv_z0", C.c_double), ("lv_z1", C.c_double), ("lv_switch", C.c_double),
+                ("pic_masked", C.c_int32), ("integrator", C.c_int32)]
 
 
 class Layout(C.Structure):
@@ -111,6 +113,8 @@ def lib():
         L.mucite_launch_count.restype = C.c_int64
         L.mucite_sync.argtypes = [vp]
         L.mucite_poisson_solve_noalloc.argtypes = [C.c_int, vp, C.POINTER(Grid), vp, vp, vp, vp]
+        L.mucite_set_dt.argtypes = [vp, C.c_int, C.c_double]
+        L.mucite_dt_limits.argtypes = [vp, C.c_int, dp]
         _lib = L
     return _lib
 
@@ -139,7 +143,7 @@ def run_struct(run):
                run.r_det, run.m_gas_da, run.seed & 0xFFFFFFFFFFFFFFFF, run.precision, run.pic_interval,
                run.exit_bin_steps, run.n_exit_bins, run.n_r_bins, run.n_ke_bins, run.n_teff_bins,
                run.n_loss_r, run.n_loss_z, run.ke_max_ev, run.teff_max, int(run.langevin), run.lv_z0, run.lv_z1,
-               run.lv_switch)
+               run.lv_switch, int(run.pic_masked), int(run.integrator))
 
 
 def state_layout(precision, capacity):
@@ -259,6 +263,15 @@ class Context:
 
     def set_tuning(self, steps_per_launch=0, threads_per_block=0):
         self._check(lib().mucite_set_tuning(self._p, int(steps_per_launch), int(threads_per_block)))
+
+    def set_dt(self, instance, dt):
+        self._check(lib().mucite_set_dt(self._p, instance, float(dt)))
+        self.meta[instance]["run"].dt = dt
+
+    def dt_limits(self, instance):
+        out = (C.c_double * 6)()
+        self._check(lib().mucite_dt_limits(self._p, instance, out))
+        return np.array(out[:])
 
     def set_launch_mode(self, persistent_blocks_per_sm=0, use_graphs=True):
         self._check(lib().mucite_set_launch_mode(self._p, int(persistent_blocks_per_sm), int(bool(use_graphs))))

@@ -119,6 +119,8 @@ class Run:
     lv_z0: float = 0.0
     lv_z1: float = 0.0
     lv_switch: float = 0.05
+    pic_masked: int = 0       # impose Phi = 0 on metal nodes of the PIC grid
+    integrator: int = 0       # 0 leapfrog, 1 RK4
     # tally histogram layout
     exit_bin_steps: int = 1000
     n_exit_bins: int = 64
