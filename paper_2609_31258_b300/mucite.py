@@ -212,7 +212,8 @@ class Context:
                                         C.byref(source_struct(source)), C.byref(run_struct(run)),
                                         C.c_void_p(pool.data_ptr()), cap))
         self.pools[instance] = (buf, pool, lay)
-        self.meta[instance] = dict(run=run, ion=ion, source=source, capacity=cap)
+        import copy
+        self.meta[instance] = dict(run=copy.copy(run), ion=ion, source=source, capacity=cap)
         return pool
 
     def release(self, instance):
