@@ -260,7 +260,7 @@ def main():
                 "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
                 "inst_per_pack_step": insts, "pack_steps_per_launch": ps_per_launch,
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
-                "hbm_bytes_per_pack_step_at_launch": 57.0 / (args.spl or 2000)}
+                "hbm_bytes_per_pack_step_at_launch": 65.0 / (args.spl or 2000)}
 
     if args.section == "fused":
         print(json.dumps({"value": value, "pack_steps_per_step": pack_steps / args.steps,

@@ -137,12 +137,16 @@ typedef struct {
 } mucite_run;
 
 /* Byte offsets of the structure-of-arrays pack pool (each array 256-byte
- * aligned). FP32: xq, yq, zq int32; vx, vy, vz, eint, lnsy float. FP64: x, y,
- * z, vx, vy, vz, eint, lnsy double. Both: status uint8, t_term int32 (step
- * count at which the pack became terminal, -1 while active). lnsy is the log
- * of the precursor survival yield of Eq. 7 (0 when dissociation is off). */
+ * aligned). FP32: xq, yq, zq int32; vx, vy, vz, eint, lnsy, tau float. FP64:
+ * x, y, z, vx, vy, vz, eint, lnsy, tau double. Both: status uint8, t_term
+ * int32 (step count at which the pack became terminal, -1 while active). lnsy
+ * is the log of the precursor survival yield of Eq. 7 (0 when dissociation
+ * is off); tau is the optical depth (an Exp(1) variate, dimensionless) left
+ * until the pack's next collision candidate, drawn at injection and consumed
+ * at the local candidate rate n sigma (|v - u| + 2 s / sqrt(pi)). */
 typedef struct {
-    int64_t off_x, off_y, off_z, off_vx, off_vy, off_vz, off_eint, off_status, off_t_term, off_lnsy;
+    int64_t off_x, off_y, off_z, off_vx, off_vy, off_vz, off_eint, off_status, off_t_term, off_lnsy,
+        off_tau;
     int64_t total_bytes;
     int32_t pos_bytes, vel_bytes;
 } mucite_layout;

@@ -92,7 +92,7 @@ class OrcRun(C.Structure):
 class OrcState(C.Structure):
     _fields_ = [("x", _dp), ("y", _dp), ("z", _dp), ("vx", _dp), ("vy", _dp), ("vz", _dp),
                 ("eint", _dp), ("status", _u8p), ("t_term", _i32p), ("ncoll", _i64p),
-                ("nsteps", _i64p), ("noverflow", _i64p), ("lnsy", _dp)]
+                ("nsteps", _i64p), ("noverflow", _i64p), ("lnsy", _dp), ("tau", _dp)]
 
 
 class OrcTally(C.Structure):
@@ -292,6 +292,7 @@ class Sim:
         self.nsteps = np.zeros(cap, np.int64)
         self.noverflow = np.zeros(cap, np.int64)
         self.lnsy = np.zeros(cap)
+        self.tau = np.zeros(cap)
         self.n = 0
         self.step = 0
         self.src_acc = 0.0
@@ -312,7 +313,8 @@ class Sim:
         return OrcState(*(_ptr(a, _dp) for a in (self.x, self.y, self.z, self.vx, self.vy, self.vz,
                                                   self.eint)),
                         _ptr(self.status, _u8p), _ptr(self.t_term, _i32p), _ptr(self.ncoll, _i64p),
-                        _ptr(self.nsteps, _i64p), _ptr(self.noverflow, _i64p), _ptr(self.lnsy, _dp))
+                        _ptr(self.nsteps, _i64p), _ptr(self.noverflow, _i64p), _ptr(self.lnsy, _dp),
+                        _ptr(self.tau, _dp))
 
     def inject(self, count=None):
         count = self.w.source.n_initial if count is None else count

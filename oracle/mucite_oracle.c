@@ -141,6 +141,7 @@ typedef struct {
     int64_t *nsteps;   /* active steps advanced per pack */
     int64_t *noverflow;/* steps where the candidate cap was reached */
     double *lnsy;      /* ln of the precursor survival yield SY (Eq. 7) */
+    double *tau;       /* optical depth left until the next collision candidate */
 } orc_state;
 
 /* ------------------------------------------------------------------------- */
@@ -304,21 +305,43 @@ double orc_rf_scalar_half(const orc_run *run, int64_t n)
 /* with c' drawn from f(c')(w + |c'|) / (w + 2s/sqrt(pi)) (a mixture of the   */
 /* Maxwellian and its speed-weighted form) and accepted with probability     */
 /* |v - c| / (w + |c'|). Accepted events occur at rate n*sigma*<|v - c|>.     */
-/* Waiting times between candidates are exponential; the rate is recomputed  */
-/* after every accepted event (null-collision sub-cycling).                  */
+/* Candidates form a Poisson process of rate nu = n sigma (w + 2s/sqrt(pi))   */
+/* (recomputed after every accepted event and at every step): each pack      */
+/* carries the optical depth tau (an Exp(1) variate) left until its next     */
+/* candidate; a step of length dt consumes nu (dt - t); when tau runs out     */
+/* inside the step a candidate is processed and a fresh tau is drawn.         */
 /*                                                                           */
 /* Accepted event: isotropic scattering in the centre-of-mass frame, momentum */
 /* conserved, internal exchange by the Borgnakke-Larsen rule: the collision  */
 /* energy E_c = mu g^2/2 + E_int is split with E_int' = B E_c,               */
 /* B ~ Beta(Cv(T_eff)/k_B, 2), sampled as U1^(1/a) U2^(1/(a+1)); 1-B is       */
 /* formed with expm1 so that small exchanges keep their precision.           */
-/* Draw blocks per candidate k: 3k (wait, branch, accept), 3k+1 (partner),   */
-/* 3k+2 (scattering direction and B).                                        */
+/* Uniforms of candidate k of a step: 12 fields of Philox blocks 2k and 2k+1 */
+/* (see draw_candidate).                                                     */
 /* Pins: collision rate vs n*sigma*gbar(w); equilibrium T_eff -> T_gas;      */
 /* Beta moments. IICT itself: parity unpinned.                               */
 /* ------------------------------------------------------------------------- */
+
+/* 12 uniforms of one candidate from Philox blocks 2k and 2k+1 of the step
+ * (purpose 0): fields 0..7 are ((w_j >> 11) + 1/2) 2^-21 of the eight words,
+ * fields 8..11 join the low 11 bits of word pairs (2m, 2m+1) into 22-bit
+ * uniforms ((v + 1/2) 2^-22). Exact in FP32 and FP64. */
+static void draw_candidate(uint64_t seed, uint32_t pack, uint32_t step, uint32_t k, double f[12])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c0[4] = {pack, step, 2u * k, 0u}, c1[4] = {pack, step, 2u * k + 1u, 0u};
+    uint32_t w[8];
+    orc_philox4x32_10(c0, key, w);
+    orc_philox4x32_10(c1, key, w + 4);
+    for (int j = 0; j < 8; ++j) f[j] = ((double)(w[j] >> 11) + 0.5) * (1.0 / 2097152.0);
+    for (int m = 0; m < 4; ++m) {
+        uint32_t v = ((w[2 * m] & 0x7FFu) << 11) | (w[2 * m + 1] & 0x7FFu);
+        f[8 + m] = ((double)v + 0.5) * (1.0 / 4194304.0);
+    }
+}
+
 static int collide(const orc_ion *ion, const orc_run *run, const orc_local *L, uint64_t seed,
-                   uint32_t pack, uint32_t step, double v[3], double *eint, int frozen,
+                   uint32_t pack, uint32_t step, double v[3], double *eint, double *tau, int frozen,
                    int *overflow)
 {
     *overflow = 0;
@@ -334,48 +357,49 @@ static int collide(const orc_ion *ion, const orc_run *run, const orc_local *L, u
         double w3[3] = {v[0] - L->u[0], v[1] - L->u[1], v[2] - L->u[2]};
         double w = sqrt(w3[0] * w3[0] + w3[1] * w3[1] + w3[2] * w3[2]);
         double nu = L->n * sigma * (w + cbar);
-        double a[4];
-        draw4(seed, pack, step, 3u * k, 0u, a);
-        t += -log(a[0]) / nu;
-        if (t >= run->dt) return accepted;
-        double b[4], cp[3], cmag;
-        draw4(seed, pack, step, 3u * k + 1u, 0u, b);
+        double room = nu * (run->dt - t);
+        if (*tau >= room) {
+            *tau -= room;
+            return accepted;
+        }
+        t += *tau / nu;
+        double f[12];
+        draw_candidate(seed, pack, step, (uint32_t)k, f);
+        *tau = -log(f[11]);
         /* Both partner laws are isotropic with |c'|^2/s^2 ~ Gamma(k, 1):
          * k = 3/2 for the Maxwellian (components of variance s^2/2), k = 2 for
          * its speed-weighted form. Gamma(2) = Exp(1) + Exp(1); Gamma(3/2) =
          * Exp(1) + N^2/2 with N = sqrt(-2 ln u) cos(2 pi u'), so
          * N^2/2 = -ln(u) cos^2(2 pi u'). */
-        double f = 1.0;
-        if (a[1] * (w + cbar) < w) {
-            double cw = cos(2.0 * ORC_PI * a[3]);
-            f = cw * cw;
+        double fk = 1.0;
+        if (f[0] * (w + cbar) < w) {
+            double cw = cos(2.0 * ORC_PI * f[2]);
+            fk = cw * cw;
         }
-        double y = -log(b[0]) - log(b[1]) * f;
-        cmag = s * sqrt(y);
-        double pct = 2.0 * b[2] - 1.0, pst = sqrt(fmax(0.0, 1.0 - pct * pct));
-        double pph = 2.0 * ORC_PI * b[3];
+        double y = -log(f[3]) - log(f[4]) * fk;
+        double cmag = s * sqrt(y), cp[3];
+        double pct = 2.0 * f[5] - 1.0, pst = sqrt(fmax(0.0, 1.0 - pct * pct));
+        double pph = 2.0 * ORC_PI * f[6];
         cp[0] = cmag * pst * cos(pph);
         cp[1] = cmag * pst * sin(pph);
         cp[2] = cmag * pct;
         double g3[3] = {w3[0] - cp[0], w3[1] - cp[1], w3[2] - cp[2]};
         double g = sqrt(g3[0] * g3[0] + g3[1] * g3[1] + g3[2] * g3[2]);
-        if (!(a[2] * (w + cmag) < g)) continue;
+        if (!(f[1] * (w + cmag) < g)) continue;
         ++accepted;
         if (frozen) continue;
-        double c[4];
-        draw4(seed, pack, step, 3u * k + 2u, 0u, c);
         double Vcm[3];
         for (int d = 0; d < 3; ++d) Vcm[d] = (M * v[d] + mg * (L->u[d] + cp[d])) / (M + mg);
         double etr = 0.5 * mu * g * g / ORC_KB; /* [K] */
         double ec = etr + *eint;
         double Teff = orc_T_of_eint(ion, *eint);
         double acv = orc_cv_of_T(ion, Teff);
-        double one_minus_B = -expm1(log(c[2]) / acv + log(c[3]) / (acv + 1.0));
+        double one_minus_B = -expm1(log(f[9]) / acv + log(f[10]) / (acv + 1.0));
         double etr_new = ec * one_minus_B;
         *eint = *eint + (etr - etr_new);
         double gnew = sqrt(2.0 * etr_new * ORC_KB / mu);
-        double ct = 2.0 * c[0] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-        double ph = 2.0 * ORC_PI * c[1];
+        double ct = 2.0 * f[7] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        double ph = 2.0 * ORC_PI * f[8];
         double nhat[3] = {st * cos(ph), st * sin(ph), ct};
         for (int d = 0; d < 3; ++d) v[d] = Vcm[d] + (mg / (M + mg)) * gnew * nhat[d];
     }
@@ -518,6 +542,7 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
         double v[3] = {S->vx[p], S->vy[p], S->vz[p]};
         double eint = S->eint[p];
         double lnsy = S->lnsy ? S->lnsy[p] : 0.0;
+        double tau = S->tau[p];
         for (int64_t k = 0; k < nsteps; ++k) {
             int64_t n = step0 + k;
             orc_local L;
@@ -528,7 +553,7 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
             if (lv)
                 langevin_step(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v);
             else
-                nc = collide(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v, &eint,
+                nc = collide(ion, run, &L, run->seed, (uint32_t)p, (uint32_t)n, v, &eint, &tau,
                              frozen_collisions, &ovf);
             if (S->ncoll) S->ncoll[p] += nc;
             if (S->noverflow) S->noverflow[p] += ovf;
@@ -574,6 +599,7 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
         S->vx[p] = v[0]; S->vy[p] = v[1]; S->vz[p] = v[2];
         S->eint[p] = eint;
         if (S->lnsy) S->lnsy[p] = lnsy;
+        S->tau[p] = tau;
     }
     free(srf);
 }
@@ -634,9 +660,11 @@ int64_t orc_count_collisions_frozen(const orc_ion *ion, const orc_run *run, doub
 #pragma omp parallel for reduction(+ : total) schedule(static)
     for (int64_t t = 0; t < trials; ++t) {
         double vv[3] = {v[0], v[1], v[2]};
-        double e = 0.0;
+        double e = 0.0, c[4];
+        draw4(run->seed, (uint32_t)t, 0u, 2u, 1u, c);
+        double tau = -log(c[0]);
         int ovf;
-        total += collide(ion, run, &L, run->seed, (uint32_t)t, (uint32_t)(t >> 32), vv, &e, 1, &ovf);
+        total += collide(ion, run, &L, run->seed, (uint32_t)t, (uint32_t)(t >> 32), vv, &e, &tau, 1, &ovf);
     }
     return total;
 }
@@ -687,6 +715,9 @@ void orc_inject(const orc_ion *ion, const orc_source *src, const orc_run *run, o
         S->status[p] = ORC_ACTIVE;
         S->t_term[p] = -1;
         if (S->lnsy) S->lnsy[p] = 0.0;
+        double c[4];
+        draw4(run->seed, (uint32_t)p, 0u, 2u, 1u, c);
+        S->tau[p] = -log(c[0]); /* Exp(1) optical depth to the first candidate */
     }
 }
 

@@ -151,6 +151,7 @@ void layout_of(int precision, int64_t cap, mucite_layout *L)
     put(L->off_status, cap);
     put(L->off_t_term, cap * 4);
     put(L->off_lnsy, cap * vb);
+    put(L->off_tau, cap * vb);
     L->total_bytes = off;
     L->pos_bytes = pb;
     L->vel_bytes = vb;
@@ -244,6 +245,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.status = at<uint8_t>(I.pool, I.lay.off_status);
         P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
         P.lnsy = at<float>(I.pool, I.lay.off_lnsy);
+        P.tau = at<float>(I.pool, I.lay.off_tau);
         }
         P.rk4 = r.integrator == 1 ? 1 : 0;
         P.rf_phase0 = I.rf_phase0;
@@ -303,6 +305,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.status = at<uint8_t>(I.pool, I.lay.off_status);
         P.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
         P.lnsy = at<double>(I.pool, I.lay.off_lnsy);
+        P.tau = at<double>(I.pool, I.lay.off_tau);
         P.tst = ion.dH_kJmol > 0.0 ? 1 : 0;
         P.tst_a = kKB / kPlanck * exp(ion.dS_JmolK / kR);
         P.tst_b = ion.dH_kJmol * 1000.0 / kR;
@@ -403,6 +406,7 @@ mucite_status inject_packs(mucite_ctx *ctx, Instance &I, int64_t p0, int64_t cou
     A.vz = (char *)I.pool + I.lay.off_vz;
     A.eint = (char *)I.pool + I.lay.off_eint;
     A.lnsy = (char *)I.pool + I.lay.off_lnsy;
+    A.tau = (char *)I.pool + I.lay.off_tau;
     A.status = at<uint8_t>(I.pool, I.lay.off_status);
     A.t_term = at<int32_t>(I.pool, I.lay.off_t_term);
     A.R = ctx->g.R;

@@ -85,6 +85,7 @@ struct Profile {
 struct InstF32 {
     int32_t *xq, *yq, *zq;
     float *vx, *vy, *vz, *eint, *lnsy;
+    float *tau;                // optical depth left until the next collision candidate
     uint8_t *status;
     int32_t *t_term;
     int64_t n_slots;
@@ -123,7 +124,7 @@ struct InstF32 {
 
 // Per-instance parameters of the plain FP64 step.
 struct InstF64 {
-    double *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy;
+    double *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy, *tau;
     uint8_t *status;
     int32_t *t_term;
     int64_t n_slots;

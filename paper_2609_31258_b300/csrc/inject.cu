@@ -2,8 +2,9 @@
 // source plane (or, for a prefill, uniformly in z), transverse position
 // uniform over a disc or from a Gaussian truncated at the hard radius
 // (inverse CDF of the truncated Rayleigh law), Maxwellian velocity at T_vel
-// with v_z folded to >= 0 on request, E_int = E_int(T_init). FP64
-// arithmetic; Philox counter (pack id, 0, block, 1).
+// with v_z folded to >= 0 on request, E_int = E_int(T_init), and the
+// Exp(1) optical depth to the first collision candidate. FP64 arithmetic;
+// Philox counter (pack id, 0, block, 1).
 #include "kernels.cuh"
 
 namespace mucite {
@@ -24,6 +25,8 @@ __global__ void inject_kernel(InjectArgs A)
     const int64_t p = A.p0 + t;
     const uint4 a = philox10(make_uint4((uint32_t)p, 0u, 0u, 1u), A.key0, A.key1);
     const uint4 b = philox10(make_uint4((uint32_t)p, 0u, 1u, 1u), A.key0, A.key1);
+    const uint4 c = philox10(make_uint4((uint32_t)p, 0u, 2u, 1u), A.key0, A.key1);
+    const double tau = -log(u01d(c.x));
     double r;
     if (A.profile == 0) {
         r = A.radius * sqrt(u01d(a.x));
@@ -51,6 +54,7 @@ __global__ void inject_kernel(InjectArgs A)
         ((float *)A.vz)[p] = (float)vz;
         ((float *)A.eint)[p] = (float)A.e0;
         ((float *)A.lnsy)[p] = 0.0f;
+        ((float *)A.tau)[p] = (float)tau;
     } else {
         ((double *)A.x)[p] = x;
         ((double *)A.y)[p] = y;
@@ -60,6 +64,7 @@ __global__ void inject_kernel(InjectArgs A)
         ((double *)A.vz)[p] = vz;
         ((double *)A.eint)[p] = A.e0;
         ((double *)A.lnsy)[p] = 0.0;
+        ((double *)A.tau)[p] = tau;
     }
     A.status[p] = MUCITE_ACTIVE;
     A.t_term[p] = -1;

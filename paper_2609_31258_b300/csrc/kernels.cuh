@@ -11,7 +11,7 @@ struct InjectArgs {
     double z_plane, radius, sigma, sd, pz0, pz1, e0;
     uint32_t key0, key1;
     int precision;
-    void *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy;
+    void *x, *y, *z, *vx, *vy, *vz, *eint, *lnsy, *tau;
     uint8_t *status;
     int32_t *t_term;
     double R, gz0, gz1;

@@ -162,29 +162,33 @@ __device__ __forceinline__ float teff_of(const InstF32 &P, float eint)
     return P.tcap + (e - P.ecap);
 }
 
-// Philox blocks of one candidate beyond the first: B (partner), C
-// (scattering and exchange) and the next candidate's A are independent, so
-// they are drawn together and their ten-round chains interleave.
-struct Blocks3 {
-    uint4 B, C, A;
-};
-
-__device__ __forceinline__ Blocks3 draw_bca(uint32_t pack, uint32_t step, uint32_t k, uint32_t k0,
-                                            uint32_t k1)
+// Uniforms of a candidate from the eight words of its two Philox blocks:
+// the top 21 bits of one word, or the low 11 bits of two words joined into
+// 22 bits; both land mid-interval and are exact in FP32.
+__device__ __forceinline__ float u21(uint32_t w)
 {
-    Blocks3 r;
-    r.B = philox10(make_uint4(pack, step, 3u * k + 1u, 0u), k0, k1);
-    r.C = philox10(make_uint4(pack, step, 3u * k + 2u, 0u), k0, k1);
-    r.A = philox10(make_uint4(pack, step, 3u * k + 3u, 0u), k0, k1);
-    return r;
+    return ((float)(w >> 11) + 0.5f) * 4.76837158203125e-07f; // 2^-21
 }
 
-// Collisions of one pack during one step of length dt, given the step's first
-// draw block A (block 0). Returns accepted events; sets *ovf when the
+__device__ __forceinline__ float u22(uint32_t hi, uint32_t lo)
+{
+    const uint32_t v = ((hi & 0x7FFu) << 11) | (lo & 0x7FFu);
+    return ((float)v + 0.5f) * 2.384185791015625e-07f; // 2^-22
+}
+
+// Collisions of one pack during one step of length dt. Candidates form a
+// Poisson process of rate nu = n sigma (|v - u| + 2 s / sqrt(pi)); the pack
+// carries the optical depth tau left until its next candidate, so a step
+// without one costs a rate evaluation and draws nothing. Candidate k of the
+// step takes Philox blocks 2k and 2k+1 (words A, B): fields A.x branch, A.y
+// accept, A.z Maxwellian extra, A.w and B.x partner magnitude, B.y and B.z
+// partner direction, B.w and (A.x, A.y low bits) scattering direction,
+// (A.z, A.w) and (B.x, B.y) low bits the Beta uniforms, (B.z, B.w) low bits
+// the next optical depth. Returns accepted events; sets *ovf when the
 // candidate cap was reached.
 __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_t pack,
-                                       uint32_t step, uint4 A, float &vx, float &vy, float &vz,
-                                       float &eint, int &ovf)
+                                       uint32_t step, float &vx, float &vy, float &vz, float &eint,
+                                       float &tau, int &ovf)
 {
     ovf = 0;
     if (!(L.nsig > 0.0f) || !(L.T > 0.0f)) return 0;
@@ -195,27 +199,33 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
     for (int k = 0; k < kKmax; ++k) {
         const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
         const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
-        t += __fdividef(-__logf(u01f(A.x)), L.nsig * (w + cbar));
-        if (t >= P.dt) return acc;
-        const Blocks3 D = draw_bca(pack, step, (uint32_t)k, P.key0, P.key1);
-        const uint4 B = D.B, Cc = D.C;
+        const float nu = L.nsig * (w + cbar);
+        const float room = nu * (P.dt - t);
+        if (tau >= room) {
+            tau -= room;
+            return acc;
+        }
+        t += __fdividef(tau, nu);
+        const uint4 A = philox10(make_uint4(pack, step, 2u * k, 0u), P.key0, P.key1);
+        const uint4 B = philox10(make_uint4(pack, step, 2u * k + 1u, 0u), P.key0, P.key1);
+        tau = -__logf(u22(B.z, B.w));
         // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
         // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
         // N^2/2 = -ln(u) cos^2(2 pi u'). One branch-free path for both laws.
         float f = 1.0f;
-        if (u01f(A.y) * (w + cbar) < w) {
+        if (u21(A.x) * (w + cbar) < w) {
             float sn0, cs0;
-            sincos_2pi(u01f(A.w), sn0, cs0);
+            sincos_2pi(u21(A.z), sn0, cs0);
             f = cs0 * cs0;
         }
-        const float y = -__logf(u01f(B.x)) - __logf(u01f(B.y)) * f;
+        const float y = -__logf(u21(A.w)) - __logf(u21(B.x)) * f;
         const float cmag = s * sqrt_fast(y);
         float cx, cy, cz;
         {
-            const float ct = 2.0f * u01f(B.z) - 1.0f;
+            const float ct = 2.0f * u21(B.y) - 1.0f;
             const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
             float sn, cs;
-            sincos_2pi(u01f(B.w), sn, cs);
+            sincos_2pi(u21(B.z), sn, cs);
             cx = cmag * st * cs;
             cy = cmag * st * sn;
             cz = cmag * ct;
@@ -223,9 +233,7 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
         const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
         const float g2 = gx * gx + gy * gy + gz * gz;
         const float g = sqrt_fast(g2);
-        const bool accept = u01f(A.z) * (w + cmag) < g;
-        A = D.A;
-        if (!accept) continue;
+        if (!(u21(A.y) * (w + cmag) < g)) continue;
         ++acc;
         const float Vx = P.fM * vx + P.fm * (L.ux + cx);
         const float Vy = P.fM * vy + P.fm * (L.uy + cy);
@@ -235,14 +243,15 @@ __device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_
         const float Te = teff_of(P, eint);
         const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
         // 1 - B for B ~ Beta(a, 2); expm1 keeps the precision of small exchanges
-        const float omb = -expm1f(__fdividef(__logf(u01f(Cc.z)), a) + __fdividef(__logf(u01f(Cc.w)), a + 1.0f));
+        const float omb = -expm1f(__fdividef(__logf(u22(A.z, A.w)), a) +
+                                  __fdividef(__logf(u22(B.x, B.y)), a + 1.0f));
         const float etr_new = ec * omb;
         eint = eint + (etr - etr_new);
         const float gn = sqrt_fast(etr_new * P.g_coef) * P.fm;
-        const float ct = 2.0f * u01f(Cc.x) - 1.0f;
+        const float ct = 2.0f * u21(B.w) - 1.0f;
         const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
         float sn, cs;
-        sincos_2pi(u01f(Cc.y), sn, cs);
+        sincos_2pi(u22(A.x, A.y), sn, cs);
         vx = Vx + gn * st * cs;
         vy = Vy + gn * st * sn;
         vz = Vz + gn * ct;
@@ -351,16 +360,13 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
         int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
         float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
         float lnsy = (kExtras && P.tst) ? P.lnsy[p] : 0.0f;
+        float tau = kCollide ? P.tau[p] : 0.0f;
         const uint32_t pack = (uint32_t)p;
         float fx = (float)xq, fy = (float)yq;
         float rr = lattice_r(fx, fy);
         int st = MUCITE_ACTIVE;
         int k = 0;
         const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
-        // first draw block of the coming step, drawn one step ahead so that its
-        // chain overlaps the kick, drift and classification of the step before
-        uint4 A0 = kCollide ? philox10(make_uint4(pack, (uint32_t)P.step0, 0u, 0u), P.key0, P.key1)
-                            : make_uint4(0u, 0u, 0u, 0u);
         for (; k < nsteps; ++k) {
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
@@ -373,10 +379,9 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
                     langevin_step(P, L, pack, n, vx, vy, vz);
                 } else {
                     int ovf;
-                    n_coll += collide(P, L, pack, n, A0, vx, vy, vz, eint, ovf);
+                    n_coll += collide(P, L, pack, n, vx, vy, vz, eint, tau, ovf);
                     n_ovf += ovf;
                 }
-                A0 = philox10(make_uint4(pack, n + 1u, 0u, 0u), P.key0, P.key1);
             }
             const float srf = s_rf[2 * k];
             const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
@@ -432,6 +437,7 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
         P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
         P.eint[p] = eint;
         if (kExtras && P.tst) P.lnsy[p] = lnsy;
+        if (kCollide) P.tau[p] = tau;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(P.step0 + k);

@@ -81,6 +81,21 @@ __device__ __forceinline__ void draw(const InstF64 &P, uint32_t pack, uint32_t s
     u[0] = u01d(o.x); u[1] = u01d(o.y); u[2] = u01d(o.z); u[3] = u01d(o.w);
 }
 
+// 12 uniforms of candidate k of a step from Philox blocks 2k and 2k+1:
+// fields 0..7 the top 21 bits of the eight words, fields 8..11 the low 11
+// bits of word pairs (0,1), (2,3), (4,5), (6,7) joined into 22 bits.
+__device__ __forceinline__ void draw_candidate(const InstF64 &P, uint32_t pack, uint32_t step, uint32_t k,
+                                               double f[12])
+{
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const uint4 a = philox10(make_uint4(pack, step, 2u * k, 0u), k0, k1);
+    const uint4 b = philox10(make_uint4(pack, step, 2u * k + 1u, 0u), k0, k1);
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    for (int j = 0; j < 8; ++j) f[j] = ((double)(w[j] >> 11) + 0.5) * 0x1p-21;
+    for (int m = 0; m < 4; ++m)
+        f[8 + m] = ((double)(((w[2 * m] & 0x7FFu) << 11) | (w[2 * m + 1] & 0x7FFu)) + 0.5) * 0x1p-22;
+}
+
 __device__ __forceinline__ double teff_d(const Profile &pf, double eint)
 {
     const double e = eint / pf.n3;
@@ -88,8 +103,10 @@ __device__ __forceinline__ double teff_d(const Profile &pf, double eint)
     return pf.tcap + (e - pf.ecap);
 }
 
+// Collisions of one pack during one step: candidates of a Poisson process of
+// rate n sigma (|v - u| + cbar) at the carried optical depth tau.
 __device__ int collide_d(const InstF64 &P, const LocalD &L, uint32_t pack, uint32_t step, double v[3],
-                         double &eint, int &ovf)
+                         double &eint, double &tau, int &ovf)
 {
     ovf = 0;
     if (!(L.n > 0.0) || !(P.sigma > 0.0) || !(L.T > 0.0)) return 0;
@@ -101,48 +118,51 @@ __device__ int collide_d(const InstF64 &P, const LocalD &L, uint32_t pack, uint3
     for (int k = 0; k < kKmax; ++k) {
         const double w3[3] = {v[0] - L.u[0], v[1] - L.u[1], v[2] - L.u[2]};
         const double w = sqrt(w3[0] * w3[0] + w3[1] * w3[1] + w3[2] * w3[2]);
-        double a[4];
-        draw(P, pack, step, 3u * k, a);
-        t += -log(a[0]) / (L.n * P.sigma * (w + cbar));
-        if (t >= P.dt) return acc;
-        double b[4], cp[3], cmag;
-        draw(P, pack, step, 3u * k + 1u, b);
+        const double nu = L.n * P.sigma * (w + cbar);
+        const double room = nu * (P.dt - t);
+        if (tau >= room) {
+            tau -= room;
+            return acc;
+        }
+        t += tau / nu;
+        double f[12];
+        draw_candidate(P, pack, step, (uint32_t)k, f);
+        tau = -log(f[11]);
         // |c'|^2 / s^2 ~ Gamma(3/2) (Maxwellian) or Gamma(2) (speed-weighted)
         double fk = 1.0;
-        if (a[1] * (w + cbar) < w) {
-            const double cw = cospi(2.0 * a[3]);
+        if (f[0] * (w + cbar) < w) {
+            const double cw = cospi(2.0 * f[2]);
             fk = cw * cw;
         }
-        const double y = -log(b[0]) - log(b[1]) * fk;
-        cmag = s * sqrt(y);
+        const double y = -log(f[3]) - log(f[4]) * fk;
+        const double cmag = s * sqrt(y);
+        double cp[3];
         {
-            const double ct = 2.0 * b[2] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            const double ct = 2.0 * f[5] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
             double sn, cs;
-            sincospi(2.0 * b[3], &sn, &cs);
+            sincospi(2.0 * f[6], &sn, &cs);
             cp[0] = cmag * st * cs;
             cp[1] = cmag * st * sn;
             cp[2] = cmag * ct;
         }
         const double g3[3] = {w3[0] - cp[0], w3[1] - cp[1], w3[2] - cp[2]};
         const double g = sqrt(g3[0] * g3[0] + g3[1] * g3[1] + g3[2] * g3[2]);
-        if (!(a[2] * (w + cmag) < g)) continue;
+        if (!(f[1] * (w + cmag) < g)) continue;
         ++acc;
-        double c[4];
-        draw(P, pack, step, 3u * k + 2u, c);
         double Vcm[3];
         for (int d = 0; d < 3; ++d) Vcm[d] = (M * v[d] + mg * (L.u[d] + cp[d])) / (M + mg);
         const double etr = 0.5 * mu * g * g / kKB;
         const double ec = etr + eint;
         const double Te = teff_d(P.prof, eint);
-        const double f = P.prof.c0 + P.prof.c1 * Te;
-        const double acv = P.prof.n3 * (f < 1.0 ? f : 1.0);
-        const double omb = -expm1(log(c[2]) / acv + log(c[3]) / (acv + 1.0));
+        const double fc = P.prof.c0 + P.prof.c1 * Te;
+        const double acv = P.prof.n3 * (fc < 1.0 ? fc : 1.0);
+        const double omb = -expm1(log(f[9]) / acv + log(f[10]) / (acv + 1.0));
         const double etr_new = ec * omb;
         eint = eint + (etr - etr_new);
         const double gnew = sqrt(2.0 * etr_new * kKB / mu);
-        const double ct = 2.0 * c[0] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        const double ct = 2.0 * f[7] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
         double sn, cs;
-        sincospi(2.0 * c[1], &sn, &cs);
+        sincospi(2.0 * f[8], &sn, &cs);
         const double nh[3] = {st * cs, st * sn, ct};
         for (int d = 0; d < 3; ++d) v[d] = Vcm[d] + (mg / (M + mg)) * gnew * nh[d];
     }
@@ -227,13 +247,14 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
         double v[3] = {P.vx[p], P.vy[p], P.vz[p]};
         double eint = P.eint[p];
         double lnsy = P.tst ? P.lnsy[p] : 0.0;
+        double tau = P.tau[p];
         LocalD L;
         gather_d(G, P, x, y, z, L);
         int ovf = 0;
         const bool lv = P.langevin && z >= P.lv_z0 && z <= P.lv_z1 &&
                         collision_rate_d(P, L, v) * P.dt >= P.lv_switch;
         if (lv) langevin_d(P, L, (uint32_t)p, (uint32_t)step, v);
-        else coll = (unsigned)collide_d(P, L, (uint32_t)p, (uint32_t)step, v, eint, ovf);
+        else coll = (unsigned)collide_d(P, L, (uint32_t)p, (uint32_t)step, v, eint, tau, ovf);
         ovf_n = (unsigned)ovf;
         if (P.tst && !lv) {
             // Eq. 7: ln SY decays at the Eyring rate of the current T_eff
@@ -267,6 +288,7 @@ __global__ void __launch_bounds__(256) step_f64_kernel(GridF64 G, InstF64 P, int
         P.vx[p] = v[0]; P.vy[p] = v[1]; P.vz[p] = v[2];
         P.eint[p] = eint;
         if (P.tst) P.lnsy[p] = lnsy;
+        P.tau[p] = tau;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(step + 1);

@@ -65,7 +65,8 @@ class Run(C.Structure):
 
 class Layout(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("off_x", "off_y", "off_z", "off_vx", "off_vy", "off_vz",
-                                         "off_eint", "off_status", "off_t_term", "off_lnsy", "total_bytes")] + \
+                                         "off_eint", "off_status", "off_t_term", "off_lnsy", "off_tau",
+                                         "total_bytes")] + \
                [("pos_bytes", C.c_int32), ("vel_bytes", C.c_int32)]
 
 
@@ -299,7 +300,8 @@ class Context:
         return dict(x=v(L.off_x, cap * ps, pt), y=v(L.off_y, cap * ps, pt), z=v(L.off_z, cap * ps, pt),
                     vx=v(L.off_vx, cap * vs, vt), vy=v(L.off_vy, cap * vs, vt), vz=v(L.off_vz, cap * vs, vt),
                     eint=v(L.off_eint, cap * vs, vt), status=v(L.off_status, cap, torch.uint8),
-                    t_term=v(L.off_t_term, cap * 4, torch.int32), lnsy=v(L.off_lnsy, cap * vs, vt))
+                    t_term=v(L.off_t_term, cap * 4, torch.int32), lnsy=v(L.off_lnsy, cap * vs, vt),
+                    tau=v(L.off_tau, cap * vs, vt))
 
 
 def poisson_solve_noalloc(device, stream, pic, Q, phi, esc, rel=None):

@@ -27,11 +27,13 @@ def fp32_state_from_oracle(sim):
     xq, yq, zq = lattice_from_fp64(g, sim.x[:n], sim.y[:n], sim.z[:n])
     st = dict(x=xq, y=yq, z=zq, vx=sim.vx[:n].astype(np.float32), vy=sim.vy[:n].astype(np.float32),
               vz=sim.vz[:n].astype(np.float32), eint=sim.eint[:n].astype(np.float32),
-              status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy(), lnsy=sim.lnsy[:n].astype(np.float32))
+              status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy(), lnsy=sim.lnsy[:n].astype(np.float32),
+              tau=sim.tau[:n].astype(np.float32))
     sim.x[:n], sim.y[:n], sim.z[:n] = fp64_from_lattice(g, xq, yq, zq)
     sim.vx[:n], sim.vy[:n], sim.vz[:n] = (st[k].astype(np.float64) for k in ("vx", "vy", "vz"))
     sim.eint[:n] = st["eint"].astype(np.float64)
     sim.lnsy[:n] = st["lnsy"].astype(np.float64)
+    sim.tau[:n] = st["tau"].astype(np.float64)
     return st
 
 
@@ -39,7 +41,8 @@ def fp64_state_from_oracle(sim):
     n = sim.n
     return dict(x=sim.x[:n].copy(), y=sim.y[:n].copy(), z=sim.z[:n].copy(), vx=sim.vx[:n].copy(),
                 vy=sim.vy[:n].copy(), vz=sim.vz[:n].copy(), eint=sim.eint[:n].copy(),
-                status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy(), lnsy=sim.lnsy[:n].copy())
+                status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy(), lnsy=sim.lnsy[:n].copy(),
+                tau=sim.tau[:n].copy())
 
 
 def upload(ctx, inst, arrays, step=0):

@@ -68,6 +68,9 @@ def test_inject_matches_oracle(mc, orc, precision):
             assert np.abs(a.astype(np.int64) - b).max() <= 1
             assert (a == b).mean() > 0.999
         assert np.allclose(got["vx"], s.vx[:3001].astype(np.float32), rtol=1e-6)
+    # Exp(1) optical depth to the first collision candidate
+    tol = 1e-13 if precision == 1 else 1e-6
+    assert np.allclose(got["tau"], s.tau[:3001].astype(got["tau"].dtype), rtol=tol)
     assert (got["status"] == 0).all() and (got["t_term"] == -1).all()
     ctx.close()
 

@@ -6,6 +6,9 @@
   axial secular frequency twice the radial one;
 - collision rate at a frozen ion velocity: n sigma gbar(w), with gbar the mean
   relative speed against a Maxwellian (closed form with erf);
+- optical depth carried across steps: at frozen velocities the accepted
+  events of each pack over many steps are Poisson with mean
+  n sigma gbar(w) N dt (mean and dispersion across packs);
 - thermalised ions: collision rate n sigma sqrt(8kT/(pi mu));
 - low-field drift: Mason-Schamp mobility K = (3q/16N) sqrt(2 pi/(mu k T))/sigma;
 - internal temperature relaxes to the gas temperature; E_int equilibrium
@@ -168,6 +171,28 @@ def _thermal_box(n_packs=2000, T_init=300.0, Ez=0.0, p=200.0, seed=3):
     w.source.half_space = 0
     w.ion = W.IonTemplate(mass_da=1000.0, charge=1, ccs_m2=300e-20, n_atoms=100, T_init=T_init)
     return w
+
+
+def test_collision_counts_poisson_across_steps(orc):
+    """Frozen velocities, uniform gas at rest, no field: each pack's
+    candidates are a Poisson process of constant rate, so whatever the step
+    boundaries the accepted count over N steps is Poisson(n sigma gbar(w) N dt).
+    A tau that is not consumed, or consumed twice, shifts the mean; candidate
+    draws shared between steps or packs raise the dispersion."""
+    w = _thermal_box(n_packs=2000, seed=11)
+    s = orc.Sim(w)
+    s.inject()
+    n_st = 3000
+    v = np.sqrt(s.vx[:s.n] ** 2 + s.vy[:s.n] ** 2 + s.vz[:s.n] ** 2)
+    s.steps(n_st, frozen=True)
+    assert (s.status[:s.n] == 0).all()
+    n = 200.0 / (KB * 300.0)
+    sg = math.sqrt(2 * KB * 300.0 / (28 * DA))
+    expect = np.array([n * w.ion.ccs_m2 * gbar(x, sg) * n_st * w.run.dt for x in v])
+    cnt = s.ncoll[:s.n].astype(np.float64)
+    assert abs(cnt.sum() / expect.sum() - 1) < 4 / math.sqrt(expect.sum()), (cnt.sum(), expect.sum())
+    disp = np.mean((cnt - expect) ** 2 / expect)
+    assert abs(disp - 1) < 4 * math.sqrt(2 / s.n), disp
 
 
 def test_thermal_collision_rate(orc):
