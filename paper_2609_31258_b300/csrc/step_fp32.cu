@@ -176,94 +176,103 @@ __device__ __forceinline__ float u22(uint32_t hi, uint32_t lo)
     return ((float)v + 0.5f) * 2.384185791015625e-07f; // 2^-22
 }
 
-// Collisions of one pack during one step of length dt. Candidates form a
-// Poisson process of rate nu = n sigma (|v - u| + 2 s / sqrt(pi)); the pack
-// carries the optical depth tau left until its next candidate, so a step
-// without one costs a rate evaluation and draws nothing. Candidate k of the
-// step takes Philox blocks 2k and 2k+1 (words A, B): fields A.x branch, A.y
-// accept, A.z Maxwellian extra, A.w and B.x partner magnitude, B.y and B.z
-// partner direction, B.w and (A.x, A.y low bits) scattering direction,
-// (A.z, A.w) and (B.x, B.y) low bits the Beta uniforms, (B.z, B.w) low bits
-// the next optical depth. Returns accepted events; sets *ovf when the
-// candidate cap was reached.
-__device__ __forceinline__ int collide(const InstF32 &P, const Local &L, uint32_t pack,
-                                       uint32_t step, float &vx, float &vy, float &vz, float &eint,
-                                       float &tau, int &ovf)
+// Gas and force of one step, gathered at the step's start position and held
+// while the step's collision candidates are processed.
+struct StepGas {
+    float kx, ky, kz;          // velocity kick (q/m)(s_dc E_DC + s_rf(n) E_RF + E_SCE) dt
+    float nsig, T, ux, uy, uz; // n sigma, gas temperature and flow
+};
+
+// Collisions (Eq. 6): candidates form a Poisson process of rate
+// nu = n sigma (|v - u| + 2 s / sqrt(pi)); the pack carries the optical depth
+// tau left until its next candidate, so a step without one costs a rate
+// evaluation and draws nothing. One pass at time t of the step: the rest of
+// the step holds nu (dt - t) of optical depth; returns true when tau runs out
+// inside it (a candidate at t + tau / nu), else consumes that depth.
+__device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &S, float vx, float vy,
+                                               float vz, float &tau, float &t)
 {
-    ovf = 0;
-    if (!(L.nsig > 0.0f) || !(L.T > 0.0f)) return 0;
-    const float s = sqrt_fast(P.s_coef * L.T);
-    const float cbar = 1.1283791670955126f * s; // 2 s / sqrt(pi)
-    float t = 0.0f;
-    int acc = 0;
-    for (int k = 0; k < kKmax; ++k) {
-        const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
-        const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
-        const float nu = L.nsig * (w + cbar);
-        const float room = nu * (P.dt - t);
-        if (tau >= room) {
-            tau -= room;
-            return acc;
-        }
-        t += __fdividef(tau, nu);
-        const uint4 A = philox10(make_uint4(pack, step, 2u * k, 0u), P.key0, P.key1);
-        const uint4 B = philox10(make_uint4(pack, step, 2u * k + 1u, 0u), P.key0, P.key1);
-        tau = -__logf(u22(B.z, B.w));
-        // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
-        // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
-        // N^2/2 = -ln(u) cos^2(2 pi u'). One branch-free path for both laws.
-        float f = 1.0f;
-        if (u21(A.x) * (w + cbar) < w) {
-            float sn0, cs0;
-            sincos_2pi(u21(A.z), sn0, cs0);
-            f = cs0 * cs0;
-        }
-        const float y = -__logf(u21(A.w)) - __logf(u21(B.x)) * f;
-        const float cmag = s * sqrt_fast(y);
-        float cx, cy, cz;
-        {
-            const float ct = 2.0f * u21(B.y) - 1.0f;
-            const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
-            float sn, cs;
-            sincos_2pi(u21(B.z), sn, cs);
-            cx = cmag * st * cs;
-            cy = cmag * st * sn;
-            cz = cmag * ct;
-        }
-        const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
-        const float g2 = gx * gx + gy * gy + gz * gz;
-        const float g = sqrt_fast(g2);
-        if (!(u21(A.y) * (w + cmag) < g)) continue;
-        ++acc;
-        const float Vx = P.fM * vx + P.fm * (L.ux + cx);
-        const float Vy = P.fM * vy + P.fm * (L.uy + cy);
-        const float Vz = P.fM * vz + P.fm * (L.uz + cz);
-        const float etr = P.mu_2kb * g2;
-        const float ec = etr + eint;
-        const float Te = teff_of(P, eint);
-        const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
-        // 1 - B for B ~ Beta(a, 2); expm1 keeps the precision of small exchanges
-        const float omb = -expm1f(__fdividef(__logf(u22(A.z, A.w)), a) +
-                                  __fdividef(__logf(u22(B.x, B.y)), a + 1.0f));
-        const float etr_new = ec * omb;
-        eint = eint + (etr - etr_new);
-        const float gn = sqrt_fast(etr_new * P.g_coef) * P.fm;
-        const float ct = 2.0f * u21(B.w) - 1.0f;
+    const float cbar = 1.1283791670955126f * sqrt_fast(P.s_coef * S.T); // 2 s / sqrt(pi)
+    const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
+    const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    const float nu = S.nsig * (w + cbar);
+    const float room = nu * (P.dt - t);
+    if (tau >= room) {
+        tau -= room;
+        return false;
+    }
+    t += __fdividef(tau, nu);
+    return true;
+}
+
+// Candidate kc of a step (Philox blocks 2kc and 2kc+1, words A and B):
+// fields A.x branch, A.y accept, A.z Maxwellian extra, A.w and B.x partner
+// magnitude, B.y and B.z partner direction, B.w and (A.x, A.y low bits)
+// scattering direction, (A.z, A.w) and (B.x, B.y) low bits the Beta uniforms,
+// (B.z, B.w) low bits the next optical depth. Returns 1 when accepted.
+__device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uint32_t pack, uint32_t step,
+                                         uint32_t kc, float &vx, float &vy, float &vz, float &eint,
+                                         float &tau)
+{
+    const float s = sqrt_fast(P.s_coef * S.T);
+    const float cbar = 1.1283791670955126f * s;
+    const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
+    const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    const uint4 A = philox10(make_uint4(pack, step, 2u * kc, 0u), P.key0, P.key1);
+    const uint4 B = philox10(make_uint4(pack, step, 2u * kc + 1u, 0u), P.key0, P.key1);
+    tau = -__logf(u22(B.z, B.w));
+    // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
+    // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
+    // N^2/2 = -ln(u) cos^2(2 pi u'). One branch-free path for both laws.
+    float f = 1.0f;
+    if (u21(A.x) * (w + cbar) < w) {
+        float sn0, cs0;
+        sincos_2pi(u21(A.z), sn0, cs0);
+        f = cs0 * cs0;
+    }
+    const float y = -__logf(u21(A.w)) - __logf(u21(B.x)) * f;
+    const float cmag = s * sqrt_fast(y);
+    float cx, cy, cz;
+    {
+        const float ct = 2.0f * u21(B.y) - 1.0f;
         const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
         float sn, cs;
-        sincos_2pi(u22(A.x, A.y), sn, cs);
-        vx = Vx + gn * st * cs;
-        vy = Vy + gn * st * sn;
-        vz = Vz + gn * ct;
+        sincos_2pi(u21(B.z), sn, cs);
+        cx = cmag * st * cs;
+        cy = cmag * st * sn;
+        cz = cmag * ct;
     }
-    ovf = 1;
-    return acc;
+    const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float g = sqrt_fast(g2);
+    if (!(u21(A.y) * (w + cmag) < g)) return 0;
+    const float Vx = P.fM * vx + P.fm * (S.ux + cx);
+    const float Vy = P.fM * vy + P.fm * (S.uy + cy);
+    const float Vz = P.fM * vz + P.fm * (S.uz + cz);
+    const float etr = P.mu_2kb * g2;
+    const float ec = etr + eint;
+    const float Te = teff_of(P, eint);
+    const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
+    // 1 - B for B ~ Beta(a, 2); expm1 keeps the precision of small exchanges
+    const float omb = -expm1f(__fdividef(__logf(u22(A.z, A.w)), a) +
+                              __fdividef(__logf(u22(B.x, B.y)), a + 1.0f));
+    const float etr_new = ec * omb;
+    eint = eint + (etr - etr_new);
+    const float gn = sqrt_fast(etr_new * P.g_coef) * P.fm;
+    const float ct = 2.0f * u21(B.w) - 1.0f;
+    const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
+    float sn, cs;
+    sincos_2pi(u22(A.x, A.y), sn, cs);
+    vx = Vx + gn * st * cs;
+    vy = Vy + gn * st * sn;
+    vz = Vz + gn * ct;
+    return 1;
 }
 
 // Expected collision rate n sigma <|v - c|> (Eq. 6, Maxwellian partner):
 // n sigma s [(x + 1/(2x)) erf(x) + exp(-x^2)/sqrt(pi)], x = |v - u| / s.
-__device__ __forceinline__ float collision_rate(const InstF32 &P, const Local &L, float vx, float vy,
-                                                float vz)
+template <class Gas>
+__device__ __forceinline__ float collision_rate(const InstF32 &P, const Gas &L, float vx, float vy, float vz)
 {
     const float s = sqrt_fast(P.s_coef * L.T);
     const float wx = vx - L.ux, wy = vy - L.uy, wz = vz - L.uz;
@@ -277,7 +286,7 @@ __device__ __forceinline__ float collision_rate(const InstF32 &P, const Local &L
 // Hybrid Langevin step: exact Ornstein-Uhlenbeck update of v - u over dt with
 // friction gamma = q / (M K) (Mason-Schamp K) and the gas temperature's
 // equilibrium spread; normals from draw block 128 of the step.
-__device__ __forceinline__ void langevin_step(const InstF32 &P, const Local &L, uint32_t pack,
+__device__ __forceinline__ void langevin_step(const InstF32 &P, const StepGas &L, uint32_t pack,
                                               uint32_t step, float &vx, float &vy, float &vz)
 {
     const float sqT = sqrt_fast(L.T);
@@ -348,19 +357,84 @@ __device__ __forceinline__ void stage_kick(const GridF32 &G, const InstF32 &P, i
     kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
 }
 
-// Advance the `blockDim.x` packs of one tile of instance P starting at pack
-// `off` by `nsteps` micro steps, and add the warp totals to the counters.
-template <bool kCollide, bool kExtras>
-__device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, const float *s_rf,
-                                         int64_t off, int nsteps)
+// Counters of a warp added to the instance's totals.
+__device__ __forceinline__ void add_counters(const InstF32 &P, unsigned n_steps_done, unsigned n_coll,
+                                             unsigned n_ovf)
+{
+    n_steps_done = warp_sum(n_steps_done);
+    n_coll = warp_sum(n_coll);
+    n_ovf = warp_sum(n_ovf);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_steps_done) atomicAdd(&P.counters[0], (unsigned long long)n_steps_done);
+        if (n_coll) atomicAdd(&P.counters[1], (unsigned long long)n_coll);
+        if (n_ovf) atomicAdd(&P.counters[2], (unsigned long long)n_ovf);
+    }
+}
+
+// Kick and drift of step n with kick (kx, ky, kz) evaluated at x_n (RK4:
+// the first stage), then the lattice radius and class at x_{n+1}.
+template <bool kExtras>
+__device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
+                                    uint32_t h1, uint32_t h2, float kx, float ky, float kz, int32_t &xq,
+                                    int32_t &yq, int32_t &zq, float &vx, float &vy, float &vz, float &fx,
+                                    float &fy, float &rr)
+{
+    if (kExtras && P.rk4) {
+        // RK4 under the instantaneous field: stages at t, t + dt/2 (x2)
+        // and t + dt; stage positions rounded to the lattice
+        const float sh = s_rf[2 * k + 1], s1 = s_rf[2 * k + 2];
+        float k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+        stage_kick(G, P, xq, yq, zq, 0.5f * vx, 0.5f * vy, 0.5f * vz, sh, k2x, k2y, k2z);
+        const float v2x = vx + 0.5f * kx, v2y = vy + 0.5f * ky, v2z = vz + 0.5f * kz;
+        stage_kick(G, P, xq, yq, zq, 0.5f * v2x, 0.5f * v2y, 0.5f * v2z, sh, k3x, k3y, k3z);
+        const float v3x = vx + 0.5f * k2x, v3y = vy + 0.5f * k2y, v3z = vz + 0.5f * k2z;
+        stage_kick(G, P, xq, yq, zq, v3x, v3y, v3z, s1, k4x, k4y, k4z);
+        const float v4x = vx + k3x, v4y = vy + k3y, v4z = vz + k3z;
+        const float c6 = 1.0f / 6.0f;
+        const float ux = (vx + 2.0f * v2x + 2.0f * v3x + v4x) * c6;
+        const float uy = (vy + 2.0f * v2y + 2.0f * v3y + v4y) * c6;
+        const float uz = (vz + 2.0f * v2z + 2.0f * v3z + v4z) * c6;
+        vx = add_sr(vx, (kx + 2.0f * k2x + 2.0f * k3x + k4x) * c6, dither(h1, 0));
+        vy = add_sr(vy, (ky + 2.0f * k2y + 2.0f * k3y + k4y) * c6, dither(h1, 11));
+        vz = add_sr(vz, (kz + 2.0f * k2z + 2.0f * k3z + k4z) * c6, dither(h1, 22));
+        xq += lattice_step(ux * P.cxs, dither(h2, 0));
+        yq += lattice_step(uy * P.cxs, dither(h2, 11));
+        zq += lattice_step(uz * P.czs, dither(h2, 22));
+    } else {
+        vx = add_sr(vx, kx, dither(h1, 0));
+        vy = add_sr(vy, ky, dither(h1, 11));
+        vz = add_sr(vz, kz, dither(h1, 22));
+        xq += lattice_step(vx * P.cxs, dither(h2, 0));
+        yq += lattice_step(vy * P.cxs, dither(h2, 11));
+        zq += lattice_step(vz * P.czs, dither(h2, 22));
+    }
+    fx = (float)xq;
+    fy = (float)yq;
+    rr = lattice_r(fx, fy);
+    return classify(G, P, xq, yq, zq, rr);
+}
+
+// Kick of step k at the gathered fields.
+__device__ __forceinline__ void kick_of(const InstF32 &P, const Local &L, float srf, float &kx, float &ky,
+                                        float &kz)
+{
+    kx = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
+    ky = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
+    kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+}
+
+// Collision-free tile: the `blockDim.x` packs of instance P starting at pack
+// `off` advance `nsteps` micro steps (gather, kick, drift, classify).
+template <bool kExtras>
+__device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P, const float *s_rf,
+                                              int64_t off, int nsteps)
 {
     const int64_t p = off + threadIdx.x;
-    unsigned n_steps_done = 0, n_coll = 0, n_ovf = 0;
+    unsigned n_steps_done = 0;
     if (p < P.n_slots && P.status[p] == MUCITE_ACTIVE) {
         int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
         float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
         float lnsy = (kExtras && P.tst) ? P.lnsy[p] : 0.0f;
-        float tau = kCollide ? P.tau[p] : 0.0f;
         const uint32_t pack = (uint32_t)p;
         float fx = (float)xq, fy = (float)yq;
         float rr = lattice_r(fx, fy);
@@ -371,62 +445,16 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
             const uint32_t n = (uint32_t)(P.step0 + k);
             Local L;
             gather(G, P, fx, fy, rr, zq, L);
-            bool lv = false;
-            if (kCollide) {
-                if (kExtras && P.langevin && zq >= P.lv_zq0 && zq <= P.lv_zq1 && L.nsig > 0.0f && L.T > 0.0f)
-                    lv = collision_rate(P, L, vx, vy, vz) * P.dt >= P.lv_switch;
-                if (lv) {
-                    langevin_step(P, L, pack, n, vx, vy, vz);
-                } else {
-                    int ovf;
-                    n_coll += collide(P, L, pack, n, vx, vy, vz, eint, tau, ovf);
-                    n_ovf += ovf;
-                }
-            }
-            const float srf = s_rf[2 * k];
+            float kx, ky, kz;
+            kick_of(P, L, s_rf[2 * k], kx, ky, kz);
             const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
-            if (kExtras && P.tst && !lv) {
+            if (kExtras && P.tst) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
                 const float Te = teff_of(P, eint);
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
                 lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
             }
-            if (kExtras && P.rk4) {
-                // RK4 under the instantaneous field: stages at t, t + dt/2 (x2)
-                // and t + dt; stage positions rounded to the lattice
-                const float sh = s_rf[2 * k + 1], s1 = s_rf[2 * k + 2];
-                const float k1x = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
-                const float k1y = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
-                const float k1z = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
-                float k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
-                stage_kick(G, P, xq, yq, zq, 0.5f * vx, 0.5f * vy, 0.5f * vz, sh, k2x, k2y, k2z);
-                const float v2x = vx + 0.5f * k1x, v2y = vy + 0.5f * k1y, v2z = vz + 0.5f * k1z;
-                stage_kick(G, P, xq, yq, zq, 0.5f * v2x, 0.5f * v2y, 0.5f * v2z, sh, k3x, k3y, k3z);
-                const float v3x = vx + 0.5f * k2x, v3y = vy + 0.5f * k2y, v3z = vz + 0.5f * k2z;
-                stage_kick(G, P, xq, yq, zq, v3x, v3y, v3z, s1, k4x, k4y, k4z);
-                const float v4x = vx + k3x, v4y = vy + k3y, v4z = vz + k3z;
-                const float c6 = 1.0f / 6.0f;
-                const float ux = (vx + 2.0f * v2x + 2.0f * v3x + v4x) * c6;
-                const float uy = (vy + 2.0f * v2y + 2.0f * v3y + v4y) * c6;
-                const float uz = (vz + 2.0f * v2z + 2.0f * v3z + v4z) * c6;
-                vx = add_sr(vx, (k1x + 2.0f * k2x + 2.0f * k3x + k4x) * c6, dither(h1, 0));
-                vy = add_sr(vy, (k1y + 2.0f * k2y + 2.0f * k3y + k4y) * c6, dither(h1, 11));
-                vz = add_sr(vz, (k1z + 2.0f * k2z + 2.0f * k3z + k4z) * c6, dither(h1, 22));
-                xq += lattice_step(ux * P.cxs, dither(h2, 0));
-                yq += lattice_step(uy * P.cxs, dither(h2, 11));
-                zq += lattice_step(uz * P.czs, dither(h2, 22));
-            } else {
-                vx = add_sr(vx, P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx), dither(h1, 0));
-                vy = add_sr(vy, P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy), dither(h1, 11));
-                vz = add_sr(vz, P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz), dither(h1, 22));
-                xq += lattice_step(vx * P.cxs, dither(h2, 0));
-                yq += lattice_step(vy * P.cxs, dither(h2, 11));
-                zq += lattice_step(vz * P.czs, dither(h2, 22));
-            }
-            fx = (float)xq;
-            fy = (float)yq;
-            rr = lattice_r(fx, fy);
-            st = classify(G, P, xq, yq, zq, rr);
+            st = push<kExtras>(G, P, s_rf, k, h1, h2, kx, ky, kz, xq, yq, zq, vx, vy, vz, fx, fy, rr);
             if (st != MUCITE_ACTIVE) {
                 ++k;
                 break;
@@ -435,22 +463,121 @@ __device__ __forceinline__ void run_tile(const GridF32 &G, const InstF32 &P, con
         n_steps_done = (unsigned)k;
         P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
         P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
-        P.eint[p] = eint;
         if (kExtras && P.tst) P.lnsy[p] = lnsy;
-        if (kCollide) P.tau[p] = tau;
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(P.step0 + k);
         }
     }
-    n_steps_done = warp_sum(n_steps_done);
-    n_coll = warp_sum(n_coll);
-    n_ovf = warp_sum(n_ovf);
-    if ((threadIdx.x & 31) == 0) {
-        if (n_steps_done) atomicAdd(&P.counters[0], (unsigned long long)n_steps_done);
-        if (n_coll) atomicAdd(&P.counters[1], (unsigned long long)n_coll);
-        if (n_ovf) atomicAdd(&P.counters[2], (unsigned long long)n_ovf);
+    add_counters(P, n_steps_done, 0u, 0u);
+}
+
+// Start of step k of one pack: gather at x_k, the step's kick, the Langevin
+// switch, and the first pass of the candidate loop. Returns whether a
+// collision candidate is pending.
+template <bool kExtras>
+__device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
+                                           uint32_t pack, float fx, float fy, float rr, int32_t zq,
+                                           float &vx, float &vy, float &vz, float &tau, float &t,
+                                           bool &lv, StepGas &S)
+{
+    Local L;
+    gather(G, P, fx, fy, rr, zq, L);
+    kick_of(P, L, s_rf[2 * k], S.kx, S.ky, S.kz);
+    S.nsig = L.nsig; S.T = L.T;
+    S.ux = L.ux; S.uy = L.uy; S.uz = L.uz;
+    t = 0.0f;
+    lv = false;
+    if (!(S.nsig > 0.0f) || !(S.T > 0.0f)) return false;
+    if (kExtras && P.langevin && zq >= P.lv_zq0 && zq <= P.lv_zq1)
+        lv = collision_rate(P, S, vx, vy, vz) * P.dt >= P.lv_switch;
+    if (lv) {
+        langevin_step(P, S, pack, (uint32_t)(P.step0 + k), vx, vy, vz);
+        return false;
     }
+    return next_candidate(P, S, vx, vy, vz, tau, t);
+}
+
+// Tile with collisions. Each lane owns a pack and walks through its steps;
+// a step may hold several collision candidates (a Poisson number). Rather
+// than stepping all lanes together, which makes the warp run the candidate
+// code as often as its busiest lane needs it, every iteration the warp
+// either processes one candidate of each lane that has one pending or
+// finishes the step (kick, drift, classify, next gather) of each lane that
+// has none, whichever serves more lanes. Lanes drift apart in step index;
+// every pack still takes exactly its own sequence of operations, so results
+// do not depend on the schedule.
+template <bool kExtras>
+__device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P, const float *s_rf,
+                                              int64_t off, int nsteps)
+{
+    const int64_t p = off + threadIdx.x;
+    const bool owned = p < P.n_slots && P.status[p] == MUCITE_ACTIVE;
+    int32_t xq = 0, yq = 0, zq = 0;
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f, eint = 0.0f, tau = 0.0f, lnsy = 0.0f;
+    if (owned) {
+        xq = P.xq[p]; yq = P.yq[p]; zq = P.zq[p];
+        vx = P.vx[p]; vy = P.vy[p]; vz = P.vz[p];
+        eint = P.eint[p];
+        tau = P.tau[p];
+        if (kExtras && P.tst) lnsy = P.lnsy[p];
+    }
+    const uint32_t pack = (uint32_t)p;
+    const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
+    float fx = (float)xq, fy = (float)yq;
+    float rr = lattice_r(fx, fy);
+    unsigned n_coll = 0, n_ovf = 0;
+    int k = 0, kc = 0, st = MUCITE_ACTIVE;
+    float t = 0.0f;
+    bool lv = false, live = owned && nsteps > 0, pend = false;
+    StepGas S;
+    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, lv, S);
+    for (;;) {
+        const bool can_push = live && !pend;
+        const unsigned mc = __ballot_sync(0xffffffffu, pend);
+        const unsigned mp = __ballot_sync(0xffffffffu, can_push);
+        if ((mc | mp) == 0u) break;
+        if (mc != 0u && __popc(mc) >= __popc(mp)) {
+            if (pend) {
+                n_coll += (unsigned)candidate(P, S, pack, (uint32_t)(P.step0 + k), (uint32_t)kc, vx, vy, vz,
+                                              eint, tau);
+                if (++kc == kKmax) {
+                    ++n_ovf; // candidate cap: the rest of the step holds no further candidate
+                    pend = false;
+                } else {
+                    pend = next_candidate(P, S, vx, vy, vz, tau, t);
+                }
+            }
+        } else if (can_push) {
+            const uint32_t n = (uint32_t)(P.step0 + k);
+            const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
+            if (kExtras && P.tst && !lv) {
+                // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
+                const float Te = teff_of(P, eint);
+                const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
+                lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
+            }
+            st = push<kExtras>(G, P, s_rf, k, h1, h2, S.kx, S.ky, S.kz, xq, yq, zq, vx, vy, vz, fx, fy, rr);
+            ++k;
+            kc = 0;
+            if (st != MUCITE_ACTIVE || k == nsteps)
+                live = false;
+            else
+                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, lv, S);
+        }
+    }
+    if (owned) {
+        P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
+        P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
+        P.eint[p] = eint;
+        P.tau[p] = tau;
+        if (kExtras && P.tst) P.lnsy[p] = lnsy;
+        if (st != MUCITE_ACTIVE) {
+            P.status[p] = (uint8_t)st;
+            P.t_term[p] = (int32_t)(P.step0 + k);
+        }
+    }
+    add_counters(P, owned ? (unsigned)k : 0u, n_coll, n_ovf);
 }
 
 } // namespace
@@ -487,7 +614,11 @@ __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF
             __syncthreads();
             cur = lo;
         }
-        run_tile<kCollide, kExtras>(G, P, s_rf, (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x, nsteps);
+        const int64_t off = (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x;
+        if (kCollide)
+            run_tile_coll<kExtras>(G, P, s_rf, off, nsteps);
+        else
+            run_tile_free<kExtras>(G, P, s_rf, off, nsteps);
     }
 }
 
