@@ -188,8 +188,9 @@ const char *mucite_last_error(const mucite_ctx *ctx);
  * distance to the metal surface [m].
  * pic: PIC grid for the space-charge field, or NULL for none; it must span
  * the same (r, z) box as `g`.
- * Errors: MUCITE_E_ARG (NULL arrays, nr < 2 or nz < 2, bad box),
- * MUCITE_E_STATE (instances already injected), MUCITE_E_OOM, MUCITE_E_CUDA. */
+ * Errors: MUCITE_E_ARG (NULL arrays, nr or nz outside [2, 2^20] (PIC grid:
+ * [3, 2^20]), more than 2^30 nodes, bad box), MUCITE_E_STATE (instances
+ * already injected), MUCITE_E_OOM, MUCITE_E_CUDA. */
 mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const double *phi_dc,
                                  const double *phi_rf_basis, const double *gas_p,
                                  const double *gas_T, const double *gas_ur, const double *gas_uz,
@@ -253,9 +254,11 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
                               float *ez, double *rel_residual);
 
 /* Launch shape of the fused FP32 step: at most `steps_per_launch` micro
- * steps are fused per launch (state stays in registers between them) with
- * `threads_per_block` threads (a multiple of 32, <= 1024). 0 keeps the
- * current value. */
+ * steps (1..6000) are fused per launch (state stays in registers between
+ * them); a block advances a tile of `threads_per_block` packs (a multiple of
+ * 64 in [64, 256]): one pack per thread with collisions, two per thread in
+ * the collision-free kernel. 0 keeps the current value; other values return
+ * MUCITE_E_ARG. */
 mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threads_per_block);
 
 /* Start a new dt segment of instance `instance` at its current step (the
@@ -277,8 +280,10 @@ mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
 /* Launch mode of the batched FP32 step (the paper runs independent cases as
  * separate processes, Supporting Information S6; here many instances share
  * one launch). persistent_blocks_per_sm > 0: a persistent launch of that many
- * blocks per SM (capped by occupancy) whose blocks take tiles of every
- * instance from a device work counter; 0: one block per tile.
+ * blocks per SM (capped by occupancy) whose blocks stride over the tiles of
+ * every instance (block b takes tiles b, b + grid, ...); 0: automatic, one
+ * block per tile for launches of more than 16 micro steps and the
+ * occupancy-sized persistent grid for shorter ones.
  * use_graphs != 0: when all stepped instances share the space-charge
  * schedule and the context stream is not the legacy default stream, one macro
  * step (PIC update, RF table, fused step, clock advance) is captured once as

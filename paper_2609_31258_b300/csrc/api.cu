@@ -584,9 +584,13 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
         extras = extras || I->f32.tst || I->f32.langevin;
     }
     int grid = total_tiles;
-    if (ctx->persistent > 0) {
-        const int per_sm =
-            std::min(ctx->persistent, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide, extras)));
+    // Launches of a few micro steps (streamed) default to an occupancy-sized
+    // grid striding over the tiles, which spares every tile the block start
+    // (descriptor copy, barriers); long fused launches default to one block
+    // per tile, so blocks whose packs finish early free their SM slot.
+    const int pers = ctx->persistent > 0 ? ctx->persistent : (chunk <= 16 ? 32 : 0);
+    if (pers > 0) {
+        const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide, extras)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
     }
     launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,
@@ -786,10 +790,11 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
     if (!g || !phi_dc || !phi_rf_basis || !gas_p || !gas_T || !gas_ur || !gas_uz || !metal_mask ||
         !surf_dist)
         return fail(ctx, MUCITE_E_ARG, "NULL field array");
-    if (g->nr < 2 || g->nz < 2 || !(g->R > 0.0) || !(g->z1 > g->z0))
+    if (g->nr < 2 || g->nz < 2 || g->nr > (1 << 20) || g->nz > (1 << 20) || !(g->R > 0.0) || !(g->z1 > g->z0))
         return fail(ctx, MUCITE_E_ARG, "bad grid (nr=%d nz=%d R=%g z0=%g z1=%g)", g->nr, g->nz, g->R,
                     g->z0, g->z1);
-    if (pic && (pic->nr < 3 || pic->nz < 3 || pic->R != g->R || pic->z0 != g->z0 || pic->z1 != g->z1))
+    if (pic && (pic->nr < 3 || pic->nz < 3 || pic->nr > (1 << 20) || pic->nz > (1 << 20) || pic->R != g->R ||
+                pic->z0 != g->z0 || pic->z1 != g->z1))
         return fail(ctx, MUCITE_E_ARG, "PIC grid must have >= 3 nodes per axis and span the static box");
     for (auto &I : ctx->inst)
         if (I.used) return fail(ctx, MUCITE_E_STATE, "release all instances before reloading fields");
@@ -1219,8 +1224,8 @@ mucite_status mucite_set_tuning(mucite_ctx *ctx, int steps_per_launch, int threa
     if (!ctx) return MUCITE_E_ARG;
     if (steps_per_launch < 0 || steps_per_launch > 6000)
         return fail(ctx, MUCITE_E_ARG, "steps_per_launch must be in [1, 6000]");
-    if (threads_per_block < 0 || threads_per_block % 32 != 0 || threads_per_block > 256)
-        return fail(ctx, MUCITE_E_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
+    if (threads_per_block < 0 || threads_per_block % 64 != 0 || threads_per_block > 256)
+        return fail(ctx, MUCITE_E_ARG, "threads_per_block must be a multiple of 64 in [64, 256]");
     drop_graph(ctx);
     if (steps_per_launch) ctx->steps_per_launch = steps_per_launch;
     if (threads_per_block) ctx->threads = threads_per_block;

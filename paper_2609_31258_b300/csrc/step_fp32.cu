@@ -40,19 +40,27 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
-// Dither in (0,1) from 10 bits of h starting at bit `sh`.
+// Dither (b + 1/2) / 1024 in (0,1) from the 10 bits b of h starting at bit
+// `sh`: b becomes the top of a mantissa in [1, 2), so no integer-to-float
+// conversion is needed; dither_c is the same value minus 1/2.
 __device__ __forceinline__ float dither(uint32_t h, int sh)
 {
-    return (float)((h >> sh) & 0x3FFu) * (1.0f / 1024.0f) + (1.0f / 2048.0f);
+    return __int_as_float(0x3F801000u | (((h >> sh) & 0x3FFu) << 13)) - 1.0f;
 }
 
-// v + d with stochastic rounding: the sum is dithered by a uniform offset of
-// one unit in the last place of the result before rounding to nearest.
-__device__ __forceinline__ float add_sr(float v, float d, float u)
+__device__ __forceinline__ float dither_c(uint32_t h, int sh)
+{
+    return __int_as_float(0x3F801000u | (((h >> sh) & 0x3FFu) << 13)) - 1.5f;
+}
+
+// v + d with stochastic rounding: the sum is dithered by a uniform offset
+// uc (centred, in (-1/2, 1/2)) of one unit in the last place of the result
+// before rounding to nearest.
+__device__ __forceinline__ float add_sr(float v, float d, float uc)
 {
     const float t = v + d;
     const float ulp = __int_as_float(__float_as_int(t) & 0x7f800000) * 1.1920928955078125e-7f;
-    return v + (d + (u - 0.5f) * ulp);
+    return v + fmaf(uc, ulp, d);
 }
 
 // sqrt where the value decides nothing discrete (approximate reciprocal root).
@@ -78,30 +86,19 @@ struct Local {
 // Cell index and fraction along one axis; clamped to the last cell.
 __device__ __forceinline__ void cell_r(float g, int n, int &i0, float &f)
 {
-    int i = __float2int_rd(g);
-    if (i > n - 2) {
-        i0 = n - 2;
-        f = 1.0f;
-    } else {
-        i0 = i;
-        f = g - (float)i;
-    }
+    const int i = __float2int_rd(g);
+    const bool last = i > n - 2;
+    i0 = last ? n - 2 : i;
+    f = last ? 1.0f : g - (float)i;
 }
 
 __device__ __forceinline__ void cell_z(int32_t zq, int n, int &j0, float &f)
 {
     const int64_t t = (int64_t)zq * (int64_t)(n - 1);
-    const int64_t j = t >> 30;
-    if (j < 0) {
-        j0 = 0;
-        f = 0.0f;
-    } else if (j > n - 2) {
-        j0 = n - 2;
-        f = 1.0f;
-    } else {
-        j0 = (int)j;
-        f = (float)(t & ((1LL << 30) - 1)) * (1.0f / 1073741824.0f);
-    }
+    const int j = (int)(t >> 30); // |zq| < 2^31 and n < 2^20: fits
+    const float fr = (float)(int)((uint32_t)t & 0x3FFFFFFFu) * (1.0f / 1073741824.0f);
+    j0 = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
+    f = j < 0 ? 0.0f : (j > n - 2 ? 1.0f : fr);
 }
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float4 c, float4 d, float w00, float w10,
@@ -129,7 +126,7 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     const float w01 = (1.0f - ar) * az, w11 = ar * az;
     const float4 fa = lerp4(a00, a10, a01, a11, w00, w10, w01, w11);
     const float4 fb = lerp4(b00, b10, b01, b11, w00, w10, w01, w11);
-    const float inv = rr > 0.0f ? __frcp_rn(rr) : 0.0f;
+    const float inv = rr > 0.0f ? __fdividef(1.0f, rr) : 0.0f;
     const float cx = fx * inv, cy = fy * inv; // Eq. 3: zero transverse projection on the axis
     L.edx = fa.x * cx; L.edy = fa.x * cy; L.edz = fa.y;
     L.erx = fa.z * cx; L.ery = fa.z * cy; L.erz = fa.w;
@@ -323,15 +320,17 @@ __device__ __forceinline__ int classify(const GridF32 &G, const InstF32 &P, int3
 {
     int ir = __float2int_rz(__fadd_rn(__fmul_rn(rr, G.sr), 0.5f));
     ir = min(ir, G.nr - 1);
-    int64_t iz = ((int64_t)zq * (int64_t)(G.nz - 1) + (1LL << 29)) >> 30;
-    iz = iz < 0 ? 0 : (iz > G.nz - 1 ? G.nz - 1 : iz);
-    const float d = __ldg(&G.dmask[(size_t)iz * G.nr + ir]);
-    if (d <= P.hit) return MUCITE_ELECTRODE;
+    // nearest z node; |zq| < 2^31 and nz < 2^20, so the shifted value fits
+    int iz = (int)(((int64_t)zq * (int64_t)(G.nz - 1) + (1LL << 29)) >> 30);
+    iz = min(max(iz, 0), G.nz - 1);
+    const float d = __ldg(&G.dmask[iz * G.nr + ir]);
     const uint64_t r2 = (uint64_t)((int64_t)xq * xq) + (uint64_t)((int64_t)yq * yq);
-    if (r2 >= (1ULL << 60)) return MUCITE_RADIAL;
-    if (zq >= P.zexit_q) return r2 <= P.rdet2 ? MUCITE_TRANSMITTED : MUCITE_AXIAL;
-    if (zq < 0) return MUCITE_AXIAL;
-    return MUCITE_ACTIVE;
+    // precedence: electrode, radial wall, exit plane (detector or not), z < 0;
+    // selected without branches, the lowest precedence first
+    int st = zq < 0 ? MUCITE_AXIAL : MUCITE_ACTIVE;
+    st = zq >= P.zexit_q ? (r2 <= P.rdet2 ? MUCITE_TRANSMITTED : MUCITE_AXIAL) : st;
+    st = r2 >= (1ULL << 60) ? MUCITE_RADIAL : st;
+    return d <= P.hit ? MUCITE_ELECTRODE : st;
 }
 
 __device__ __forceinline__ unsigned warp_sum(unsigned v)
@@ -394,16 +393,16 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
         const float ux = (vx + 2.0f * v2x + 2.0f * v3x + v4x) * c6;
         const float uy = (vy + 2.0f * v2y + 2.0f * v3y + v4y) * c6;
         const float uz = (vz + 2.0f * v2z + 2.0f * v3z + v4z) * c6;
-        vx = add_sr(vx, (kx + 2.0f * k2x + 2.0f * k3x + k4x) * c6, dither(h1, 0));
-        vy = add_sr(vy, (ky + 2.0f * k2y + 2.0f * k3y + k4y) * c6, dither(h1, 11));
-        vz = add_sr(vz, (kz + 2.0f * k2z + 2.0f * k3z + k4z) * c6, dither(h1, 22));
+        vx = add_sr(vx, (kx + 2.0f * k2x + 2.0f * k3x + k4x) * c6, dither_c(h1, 0));
+        vy = add_sr(vy, (ky + 2.0f * k2y + 2.0f * k3y + k4y) * c6, dither_c(h1, 11));
+        vz = add_sr(vz, (kz + 2.0f * k2z + 2.0f * k3z + k4z) * c6, dither_c(h1, 22));
         xq += lattice_step(ux * P.cxs, dither(h2, 0));
         yq += lattice_step(uy * P.cxs, dither(h2, 11));
         zq += lattice_step(uz * P.czs, dither(h2, 22));
     } else {
-        vx = add_sr(vx, kx, dither(h1, 0));
-        vy = add_sr(vy, ky, dither(h1, 11));
-        vz = add_sr(vz, kz, dither(h1, 22));
+        vx = add_sr(vx, kx, dither_c(h1, 0));
+        vy = add_sr(vy, ky, dither_c(h1, 11));
+        vz = add_sr(vz, kz, dither_c(h1, 22));
         xq += lattice_step(vx * P.cxs, dither(h2, 0));
         yq += lattice_step(vy * P.cxs, dither(h2, 11));
         zq += lattice_step(vz * P.czs, dither(h2, 22));
@@ -423,50 +422,83 @@ __device__ __forceinline__ void kick_of(const InstF32 &P, const Local &L, float 
     kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
 }
 
-// Collision-free tile: the `blockDim.x` packs of instance P starting at pack
-// `off` advance `nsteps` micro steps (gather, kick, drift, classify).
-template <bool kExtras>
+// Collision-free tile: the U x blockDim.x packs of instance P starting at
+// pack `off` advance `nsteps` micro steps (gather, kick, drift, classify).
+// Each thread carries U packs whose steps are computed side by side (no
+// branch between them, so their load and arithmetic chains overlap); a pack
+// that has become terminal keeps its state and only its tentative step is
+// discarded. The state of all U packs is loaded up front, not behind the
+// status load, so the loads of a thread are in flight together.
+template <bool kExtras, int U>
 __device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P, const float *s_rf,
                                               int64_t off, int nsteps)
 {
-    const int64_t p = off + threadIdx.x;
-    unsigned n_steps_done = 0;
-    if (p < P.n_slots && P.status[p] == MUCITE_ACTIVE) {
-        int32_t xq = P.xq[p], yq = P.yq[p], zq = P.zq[p];
-        float vx = P.vx[p], vy = P.vy[p], vz = P.vz[p], eint = P.eint[p];
-        float lnsy = (kExtras && P.tst) ? P.lnsy[p] : 0.0f;
-        const uint32_t pack = (uint32_t)p;
-        float fx = (float)xq, fy = (float)yq;
-        float rr = lattice_r(fx, fy);
-        int st = MUCITE_ACTIVE;
-        int k = 0;
-        const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
-        for (; k < nsteps; ++k) {
-            const uint32_t n = (uint32_t)(P.step0 + k);
+    int32_t xq[U], yq[U], zq[U], kd[U], st[U];
+    float vx[U], vy[U], vz[U], eint[U], lnsy[U], fx[U], fy[U], rr[U];
+    uint32_t hb[U];
+    bool own[U], mv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t p = off + threadIdx.x + (int64_t)u * blockDim.x;
+        const int64_t q = p < P.n_slots ? p : 0; // an owned slot for the unconditional loads
+        own[u] = p < P.n_slots && P.status[q] == MUCITE_ACTIVE;
+        mv[u] = own[u];
+        xq[u] = P.xq[q]; yq[u] = P.yq[q]; zq[u] = P.zq[q];
+        vx[u] = P.vx[q]; vy[u] = P.vy[q]; vz[u] = P.vz[q];
+        eint[u] = (kExtras && P.tst) ? P.eint[q] : 0.0f;
+        lnsy[u] = (kExtras && P.tst) ? P.lnsy[q] : 0.0f;
+        hb[u] = fmix32((uint32_t)p ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
+        fx[u] = (float)xq[u];
+        fy[u] = (float)yq[u];
+        rr[u] = lattice_r(fx[u], fy[u]);
+        kd[u] = 0;
+        st[u] = MUCITE_ACTIVE;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        const uint32_t n = (uint32_t)(P.step0 + k);
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             Local L;
-            gather(G, P, fx, fy, rr, zq, L);
+            gather(G, P, fx[u], fy[u], rr[u], zq[u], L);
             float kx, ky, kz;
             kick_of(P, L, s_rf[2 * k], kx, ky, kz);
-            const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
+            const uint32_t h1 = fmix32(hb[u] + 2u * n), h2 = fmix32(hb[u] + 2u * n + 1u);
+            float ls = lnsy[u];
             if (kExtras && P.tst) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
-                const float Te = teff_of(P, eint);
+                const float Te = teff_of(P, eint[u]);
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
-                lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
+                ls = add_sr(ls, -kdt, dither_c(fmix32(h1 ^ 0x68E31DA4u), 0));
             }
-            st = push<kExtras>(G, P, s_rf, k, h1, h2, kx, ky, kz, xq, yq, zq, vx, vy, vz, fx, fy, rr);
-            if (st != MUCITE_ACTIVE) {
-                ++k;
-                break;
+            int32_t x2 = xq[u], y2 = yq[u], z2 = zq[u];
+            float wx = vx[u], wy = vy[u], wz = vz[u], gx, gy, gr;
+            const int s2 = push<kExtras>(G, P, s_rf, k, h1, h2, kx, ky, kz, x2, y2, z2, wx, wy, wz, gx, gy, gr);
+            if (mv[u]) {
+                xq[u] = x2; yq[u] = y2; zq[u] = z2;
+                vx[u] = wx; vy[u] = wy; vz[u] = wz;
+                fx[u] = gx; fy[u] = gy; rr[u] = gr;
+                lnsy[u] = ls;
+                st[u] = s2;
+                kd[u] = k + 1;
+                mv[u] = s2 == MUCITE_ACTIVE;
             }
+            any = any || mv[u];
         }
-        n_steps_done = (unsigned)k;
-        P.xq[p] = xq; P.yq[p] = yq; P.zq[p] = zq;
-        P.vx[p] = vx; P.vy[p] = vy; P.vz[p] = vz;
-        if (kExtras && P.tst) P.lnsy[p] = lnsy;
-        if (st != MUCITE_ACTIVE) {
-            P.status[p] = (uint8_t)st;
-            P.t_term[p] = (int32_t)(P.step0 + k);
+        if (!any) break;
+    }
+    unsigned n_steps_done = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (!own[u]) continue;
+        const int64_t p = off + threadIdx.x + (int64_t)u * blockDim.x;
+        n_steps_done += (unsigned)kd[u];
+        P.xq[p] = xq[u]; P.yq[p] = yq[u]; P.zq[p] = zq[u];
+        P.vx[p] = vx[u]; P.vy[p] = vy[u]; P.vz[p] = vz[u];
+        if (kExtras && P.tst) P.lnsy[p] = lnsy[u];
+        if (st[u] != MUCITE_ACTIVE) {
+            P.status[p] = (uint8_t)st[u];
+            P.t_term[p] = (int32_t)(P.step0 + kd[u]);
         }
     }
     add_counters(P, n_steps_done, 0u, 0u);
@@ -555,7 +587,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
                 const float Te = teff_of(P, eint);
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
-                lnsy = add_sr(lnsy, -kdt, dither(fmix32(h1 ^ 0x68E31DA4u), 0));
+                lnsy = add_sr(lnsy, -kdt, dither_c(fmix32(h1 ^ 0x68E31DA4u), 0));
             }
             st = push<kExtras>(G, P, s_rf, k, h1, h2, S.kx, S.ky, S.kz, xq, yq, zq, vx, vy, vz, fx, fy, rr);
             ++k;
@@ -588,8 +620,13 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
 // the list; a persistent grid strides over it). Every thread finds its tile's
 // instance itself; the block copies the instance descriptor and its RF
 // scalars (rf_table_kernel) into shared memory only when the instance changes.
+// Packs per thread of the collision-free kernel (launched with
+// threads / kFreeU threads per block over the same tiles).
+constexpr int kFreeU = 2;
+
 template <bool kCollide, bool kExtras>
-__global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF32 *insts,
+__global__ void __launch_bounds__(kCollide ? 256 : 128, kCollide ? 3 : 6)
+    step_f32_kernel(GridF32 G, const InstF32 *insts,
                                                        const int32_t *tile_start, int n_inst,
                                                        int total_tiles, int nsteps)
 {
@@ -614,11 +651,12 @@ __global__ void __launch_bounds__(256, 3) step_f32_kernel(GridF32 G, const InstF
             __syncthreads();
             cur = lo;
         }
-        const int64_t off = (int64_t)(t - __ldg(&tile_start[lo])) * blockDim.x;
+        constexpr int kU = kCollide ? 1 : kFreeU;
+        const int64_t off = (int64_t)(t - __ldg(&tile_start[lo])) * (kU * blockDim.x);
         if (kCollide)
             run_tile_coll<kExtras>(G, P, s_rf, off, nsteps);
         else
-            run_tile_free<kExtras>(G, P, s_rf, off, nsteps);
+            run_tile_free<kExtras, kU>(G, P, s_rf, off, nsteps);
     }
 }
 
@@ -658,9 +696,11 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
     else if (collide)
         step_f32_kernel<true, false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
     else if (extras)
-        step_f32_kernel<false, true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+        step_f32_kernel<false, true><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
+                                                                           total_tiles, nsteps);
     else
-        step_f32_kernel<false, false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+        step_f32_kernel<false, false><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
+                                                                            total_tiles, nsteps);
 }
 
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)
@@ -677,9 +717,9 @@ int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras)
     else if (collide)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, false>, threads, smem);
     else if (extras)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, true>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, true>, threads / kFreeU, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false>, threads / kFreeU, smem);
     return b;
 }
 

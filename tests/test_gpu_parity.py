@@ -392,6 +392,10 @@ def test_edge_cases_and_errors(mc, orc):
     with pytest.raises(mc.MuciteError) as e:
         ctx.step(0, -1)
     assert e.value.status == mc.E_ARG
+    for spl, threads in ((100, 96), (100, 512), (7000, 128)):
+        with pytest.raises(mc.MuciteError) as e:
+            ctx.set_tuning(spl, threads)
+        assert e.value.status == mc.E_ARG
     bad = W.ring_stack(n_packs=10, n_steps=0, nr=129, nz=513)
     bad.source.n_initial = 10
     with pytest.raises(mc.MuciteError) as e:
