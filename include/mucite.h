@@ -228,9 +228,20 @@ mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int6
  * instance = -1. With space charge on, a PIC update runs whenever the
  * instance clock is a multiple of pic_interval before the next micro step.
  * Per micro step and active pack: gather -> collisions -> kick -> drift ->
- * classify. Random draws: counter (pack id, step, 3k + b, 0) for candidate k.
+ * classify. Random draws: candidate k of a step uses Philox blocks
+ * (pack id, step, 2k, 0) and (pack id, step, 2k + 1, 0); the optical depth
+ * to the next candidate is carried per pack (layout array tau).
  * Errors: MUCITE_E_ARG (n_steps < 0), MUCITE_E_STATE, MUCITE_E_CUDA. */
 mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps);
+
+/* Advance the `count` instances listed in `instances` (host array, each
+ * injected and listed once) by `n_steps` micro steps together: the FP32 ones
+ * in one batched launch per chunk, as mucite_step(-1) does for all. No
+ * counterpart in the paper (which runs cases as separate processes): it lets
+ * a serving loop choose which admitted requests share the next launch.
+ * Errors: MUCITE_E_ARG (n_steps < 0, count < 0, NULL list, an instance
+ * listed twice), MUCITE_E_STATE (an instance not injected), MUCITE_E_CUDA. */
+mucite_status mucite_step_set(mucite_ctx *ctx, const int *instances, int count, int n_steps);
 
 /* Space-charge macro step of one instance: int64 CIC deposit of q*W in units
  * of e * 2^-30 -> finite-volume cylindrical Poisson (dPhi/dr = 0 on the

@@ -1042,19 +1042,11 @@ mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int6
     return MUCITE_OK;
 }
 
-mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps)
+namespace {
+
+// Advance the selected instances together (see mucite_step).
+mucite_status step_selected(mucite_ctx *ctx, const std::vector<Instance *> &sel, int n_steps)
 {
-    if (!ctx) return MUCITE_E_ARG;
-    if (n_steps < 0) return fail(ctx, MUCITE_E_ARG, "n_steps < 0");
-    std::vector<Instance *> sel;
-    if (instance == -1) {
-        for (auto &I : ctx->inst)
-            if (I.used) sel.push_back(&I);
-    } else {
-        const mucite_status st = check_instance(ctx, instance);
-        if (st != MUCITE_OK) return st;
-        sel.push_back(&ctx->inst[instance]);
-    }
     DevGuard dg(ctx->device);
     // continuous source: release the packs accumulated over this call's steps
     for (Instance *I : sel) {
@@ -1090,6 +1082,41 @@ mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps)
         }
     }
     return MUCITE_OK;
+}
+
+} // namespace
+
+mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (n_steps < 0) return fail(ctx, MUCITE_E_ARG, "n_steps < 0");
+    std::vector<Instance *> sel;
+    if (instance == -1) {
+        for (auto &I : ctx->inst)
+            if (I.used) sel.push_back(&I);
+    } else {
+        const mucite_status st = check_instance(ctx, instance);
+        if (st != MUCITE_OK) return st;
+        sel.push_back(&ctx->inst[instance]);
+    }
+    return step_selected(ctx, sel, n_steps);
+}
+
+mucite_status mucite_step_set(mucite_ctx *ctx, const int *instances, int count, int n_steps)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (n_steps < 0) return fail(ctx, MUCITE_E_ARG, "n_steps < 0");
+    if (count < 0 || (count > 0 && !instances)) return fail(ctx, MUCITE_E_ARG, "bad instance list");
+    std::vector<Instance *> sel;
+    std::vector<bool> seen(MUCITE_MAX_INSTANCES, false);
+    for (int k = 0; k < count; ++k) {
+        const mucite_status st = check_instance(ctx, instances[k]);
+        if (st != MUCITE_OK) return st;
+        if (seen[instances[k]]) return fail(ctx, MUCITE_E_ARG, "instance %d listed twice", instances[k]);
+        seen[instances[k]] = true;
+        sel.push_back(&ctx->inst[instances[k]]);
+    }
+    return step_selected(ctx, sel, n_steps);
 }
 
 mucite_status mucite_pic_update(mucite_ctx *ctx, int instance)

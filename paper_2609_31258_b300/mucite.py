@@ -22,6 +22,7 @@ MAX_INSTANCES = 256
 
 EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_fields",
            "mucite_state_layout", "mucite_inject", "mucite_release", "mucite_resume", "mucite_step",
+           "mucite_step_set",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
            "mucite_dt_limits"]
@@ -105,6 +106,7 @@ def lib():
         L.mucite_release.argtypes = [vp, C.c_int]
         L.mucite_resume.argtypes = [vp, C.c_int, C.c_int64, C.c_int64]
         L.mucite_step.argtypes = [vp, C.c_int, C.c_int]
+        L.mucite_step_set.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.c_int]
         L.mucite_pic_update.argtypes = [vp, C.c_int]
         L.mucite_tally.argtypes = [vp, C.c_int, C.POINTER(TallyOut)]
         L.mucite_pic_read.argtypes = [vp, C.c_int, _i64p, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), dp]
@@ -227,6 +229,11 @@ class Context:
 
     def step(self, instance, n_steps):
         self._check(lib().mucite_step(self._p, instance, int(n_steps)))
+
+    def step_set(self, instances, n_steps):
+        """Advance the listed instances together (one batched launch per chunk)."""
+        arr = (C.c_int * len(instances))(*[int(i) for i in instances])
+        self._check(lib().mucite_step_set(self._p, arr, len(instances), int(n_steps)))
 
     def pic_update(self, instance):
         self._check(lib().mucite_pic_update(self._p, instance))

@@ -9,9 +9,17 @@ when its clock reaches its duration it is tallied, its slot and pool are
 released, and its latency (finish - arrival) is recorded. Arrival times are
 wall-clock seconds from the start of `run`.
 
+Which admitted requests share the next launch is the batch policy: "all"
+steps every admitted request each chunk (all finish together when their
+durations agree); "srpt" takes the requests with the least remaining work
+(packs x remaining micro steps) first, adding requests until the launch
+holds at least `min_packs` packs (enough to fill the GPU), and adds any
+request that has waited longer than `max_defer` seconds for a step, so
+small requests finish early without starving large ones.
+
 Every request keeps its own Philox key (its seed) and its own clock, and
 per-pack arithmetic does not depend on the other packs of a launch, so a
-request's result is the same alone and in any mix.
+request's result is the same alone and in any mix, under either policy.
 """
 from __future__ import annotations
 
@@ -51,14 +59,41 @@ def make_request(rid, arrival, n_packs, template, base: W.Workload, n_steps, see
     return Request(rid, float(arrival), int(n_packs), template, run, src, int(n_steps))
 
 
+def srpt_batch(active, clock, min_packs, waited=None, max_defer=None):
+    """Slots to step next: shortest remaining work first (packs x remaining
+    micro steps; ties by slot), until the selection holds `min_packs` packs,
+    plus every slot whose wait since its last step exceeds `max_defer`."""
+    order = sorted(active, key=lambda s: (active[s].n_packs * (active[s].n_steps - clock[s]), s))
+    sel, packs = [], 0
+    for s in order:
+        if packs >= min_packs:
+            break
+        sel.append(s)
+        packs += active[s].n_packs
+    if waited is not None and max_defer is not None:
+        sel += [s for s in order[len(sel):] if waited[s] > max_defer]
+    return sel
+
+
 class Server:
-    def __init__(self, ctx: mucite.Context, max_slots=32, chunk=2000, mem_reserve=2 << 30):
+    def __init__(self, ctx: mucite.Context, max_slots=32, chunk=2000, mem_reserve=2 << 30, policy="srpt",
+                 min_packs=None, max_defer=5.0):
         self.ctx = ctx
         self.max_slots = min(max_slots, mucite.MAX_INSTANCES)
         self.chunk = chunk
         self.mem_reserve = mem_reserve
+        if policy not in ("all", "srpt"):
+            raise ValueError(f"unknown batch policy {policy!r}")
+        self.policy = policy
+        if min_packs is None:
+            import torch
+            # two waves of the fused collision kernel (256 threads x 3 blocks per SM)
+            min_packs = 2 * 768 * torch.cuda.get_device_properties(ctx.device).multi_processor_count
+        self.min_packs = int(min_packs)
+        self.max_defer = max_defer
         self.active = {}
         self.clock = {}
+        self.last_step = {}
         self.pack_steps = 0
 
     def _fits(self, req):
@@ -73,6 +108,7 @@ class Server:
         req.slot, req.admitted = slot, now
         self.active[slot] = req
         self.clock[slot] = 0
+        self.last_step[slot] = now
 
     def _retire(self, slot, now):
         req = self.active.pop(slot)
@@ -81,6 +117,7 @@ class Server:
         req.finished = now
         self.ctx.release(slot)
         self.clock.pop(slot)
+        self.last_step.pop(slot)
         return req
 
     def run(self, requests: List[Request], t_limit: Optional[float] = None):
@@ -98,11 +135,17 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.05)))
                 continue
-            step = min(self.chunk, min(r.n_steps - self.clock[s] for s, r in self.active.items()))
-            self.ctx.step(-1, step)
-            for s in self.active:
+            if self.policy == "srpt":
+                waited = {s: now - self.last_step[s] for s in self.active}
+                sel = srpt_batch(self.active, self.clock, self.min_packs, waited, self.max_defer)
+            else:
+                sel = sorted(self.active)
+            step = min(self.chunk, min(self.active[s].n_steps - self.clock[s] for s in sel))
+            self.ctx.step_set(sel, step)
+            for s in sel:
                 self.clock[s] += step
-            finished = [s for s, r in self.active.items() if self.clock[s] >= r.n_steps]
+                self.last_step[s] = now
+            finished = [s for s in sel if self.clock[s] >= self.active[s].n_steps]
             if finished:
                 self.ctx.sync()
                 now = time.perf_counter() - t0

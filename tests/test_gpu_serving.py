@@ -9,7 +9,8 @@ from paper_2609_31258_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_serving_mix_equals_alone():
+@pytest.mark.parametrize("policy", ["all", "srpt"])
+def test_serving_mix_equals_alone(policy):
     from paper_2609_31258_b300 import build, mucite, serving
     build.build()
     base = W.ring_stack(n_packs=1, n_steps=0, nr=129, nz=513)
@@ -21,7 +22,8 @@ def test_serving_mix_equals_alone():
     ctx.load_fields(base.fields)
     reqs = [serving.make_request(i, t, n, tmpl[k], base, n_steps=3000, seed=sd)
             for i, (t, n, k, sd) in enumerate(spec)]
-    srv = serving.Server(ctx, max_slots=3, chunk=500)
+    # srpt with a small fill: launches take subsets of the admitted requests
+    srv = serving.Server(ctx, max_slots=3, chunk=500, policy=policy, min_packs=4000, max_defer=0.5)
     done, wall = srv.run(reqs)
     assert len(done) == len(reqs)
     assert max(len(srv.active), 0) == 0
@@ -42,3 +44,31 @@ def test_serving_mix_equals_alone():
         assert np.allclose(r.tally["sum_w_ke"], T["sum_w_ke"], rtol=1e-12)
         assert np.allclose(r.tally["sum_w_teff"], T["sum_w_teff"], rtol=1e-12)
     ctx.close()
+
+
+def test_step_set_matches_step_all_and_rejects_bad_lists():
+    from paper_2609_31258_b300 import build, mucite
+    build.build()
+    w = W.ring_stack(n_packs=2000, n_steps=0, nr=129, nz=513)
+    outs = []
+    for mode in ("all", "set"):
+        ctx = mucite.Context(0)
+        ctx.set_tuning(300, 128)
+        ctx.load_fields(w.fields)
+        for i in range(3):
+            ctx.inject(i, w.ion, w.source, w.run, capacity=2000)
+        if mode == "all":
+            ctx.step(-1, 900)
+        else:
+            ctx.step_set([2, 0], 900)
+            ctx.step_set([1], 900)
+        outs.append([ctx.tally(i) for i in range(3)])
+        if mode == "set":
+            for bad in ([0, 0], [5]):
+                with pytest.raises(mucite.MuciteError) as e:
+                    ctx.step_set(bad, 10)
+                assert e.value.status in (mucite.E_ARG, mucite.E_STATE)
+        ctx.close()
+    for a, b in zip(*outs):
+        assert (a["count"] == b["count"]).all() and a["pack_steps"] == b["pack_steps"]
+        assert a["collisions"] == b["collisions"]
