@@ -26,19 +26,35 @@ constexpr int kKmax = 32;                  // collision candidates examined per 
 // multipliers, the key advanced by the two Weyl increments between rounds.
 // Counter = (pack id, step, draw block, purpose); key = (seed lo, seed hi).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_round(uint4 &c, uint32_t k0, uint32_t k1)
+{
+    // each product as one 32 x 32 -> 64-bit multiply
+    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
+    const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        philox_round(c, k0, k1);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
     return c;
+}
+
+// Two blocks under the same key, rounds interleaved (one key schedule).
+__device__ __forceinline__ void philox10x2(uint4 &a, uint4 &b, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        philox_round(a, k0, k1);
+        philox_round(b, k0, k1);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
 }
 
 // 23-bit uniform in (0,1): ((x >> 9) + 1/2) * 2^-23, exact in FP32 and FP64.

@@ -151,6 +151,16 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     }
 }
 
+// e^x - 1 for x <= 0 without cancellation: near 0 the Taylor series to x^5
+// (truncation below 1.4e-9 relative for |x| < 1/16), else expf(x) - 1,
+// whose rounding error is then small against |e^x - 1| >= 0.06.
+__device__ __forceinline__ float expm1_neg(float x)
+{
+    if (x > -0.0625f)
+        return x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f)))));
+    return expf(x) - 1.0f;
+}
+
 // T_eff from E_int (kelvin units) through the heat-capacity profile.
 __device__ __forceinline__ float teff_of(const InstF32 &P, float eint)
 {
@@ -215,8 +225,8 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     const float cbar = 1.1283791670955126f * s;
     const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
     const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
-    const uint4 A = philox10(make_uint4(pack, step, 2u * kc, 0u), P.key0, P.key1);
-    const uint4 B = philox10(make_uint4(pack, step, 2u * kc + 1u, 0u), P.key0, P.key1);
+    uint4 A = make_uint4(pack, step, 2u * kc, 0u), B = make_uint4(pack, step, 2u * kc + 1u, 0u);
+    philox10x2(A, B, P.key0, P.key1);
     tau = -__logf(u22(B.z, B.w));
     // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
     // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
@@ -251,8 +261,8 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     const float Te = teff_of(P, eint);
     const float a = P.n3 * fminf(1.0f, P.c0 + P.c1 * Te);
     // 1 - B for B ~ Beta(a, 2); expm1 keeps the precision of small exchanges
-    const float omb = -expm1f(__fdividef(__logf(u22(A.z, A.w)), a) +
-                              __fdividef(__logf(u22(B.x, B.y)), a + 1.0f));
+    const float omb = -expm1_neg(__fdividef(__logf(u22(A.z, A.w)), a) +
+                                 __fdividef(__logf(u22(B.x, B.y)), a + 1.0f));
     const float etr_new = ec * omb;
     eint = eint + (etr - etr_new);
     const float gn = sqrt_fast(etr_new * P.g_coef) * P.fm;
