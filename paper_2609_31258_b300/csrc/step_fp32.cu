@@ -78,10 +78,24 @@ __device__ __forceinline__ void sincos_2pi(float u, float &sn, float &cs)
     cs = -cs;
 }
 
+// Fields gathered at one position: radial and axial components of E_DC, of
+// the RF basis field and of E_SCE, the transverse projection (cx, cy) =
+// (x, y) / r (zero on the axis, Eq. 3), and the gas.
 struct Local {
-    float edx, edy, edz, erx, ery, erz, esx, esy, esz;
+    float edr, edz, err, erz, esr, esz, cx, cy;
     float nsig, T, ux, uy, uz;
 };
+
+// Velocity increment (a m/s per unit field) from the gathered fields: the
+// total field (Eq. 3-4) formed in (r, z) and projected once.
+__device__ __forceinline__ void field_kick(const Local &L, float a, float dc, float srf, float &kx, float &ky,
+                                           float &kz)
+{
+    const float kr = a * (dc * L.edr + srf * L.err + L.esr);
+    kx = kr * L.cx;
+    ky = kr * L.cy;
+    kz = a * (dc * L.edz + srf * L.erz + L.esz);
+}
 
 // Cell index and fraction along one axis; clamped to the last cell.
 __device__ __forceinline__ void cell_r(float g, int n, int &i0, float &f)
@@ -128,12 +142,14 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     const float4 fb = lerp4(b00, b10, b01, b11, w00, w10, w01, w11);
     const float inv = rr > 0.0f ? __fdividef(1.0f, rr) : 0.0f;
     const float cx = fx * inv, cy = fy * inv; // Eq. 3: zero transverse projection on the axis
-    L.edx = fa.x * cx; L.edy = fa.x * cy; L.edz = fa.y;
-    L.erx = fa.z * cx; L.ery = fa.z * cy; L.erz = fa.w;
+    L.cx = cx;
+    L.cy = cy;
+    L.edr = fa.x; L.edz = fa.y;
+    L.err = fa.z; L.erz = fa.w;
     L.T = fb.y;
     L.nsig = fb.y > 0.0f ? __fdividef(P.psig * fb.x, fb.y) : 0.0f;
     L.ux = fb.z * cx; L.uy = fb.z * cy; L.uz = fb.w;
-    L.esx = L.esy = L.esz = 0.0f;
+    L.esr = L.esz = 0.0f;
     if (P.esc != nullptr) {
         int pi0, pj0;
         float pr, pz;
@@ -144,10 +160,8 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
                      e11 = __ldg(&e[P.pnr + 1]);
         const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
                     v11 = pr * pz;
-        const float er = v00 * e00.x + v10 * e10.x + v01 * e01.x + v11 * e11.x;
+        L.esr = v00 * e00.x + v10 * e10.x + v01 * e01.x + v11 * e11.x;
         L.esz = v00 * e00.y + v10 * e10.y + v01 * e01.y + v11 * e11.y;
-        L.esx = er * cx;
-        L.esy = er * cy;
     }
 }
 
@@ -361,9 +375,7 @@ __device__ __forceinline__ void stage_kick(const GridF32 &G, const InstF32 &P, i
     const float fx = (float)sx, fy = (float)sy;
     Local L;
     gather(G, P, fx, fy, lattice_r(fx, fy), sz, L);
-    kx = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
-    ky = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
-    kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+    field_kick(L, P.kick, P.dc_scale, srf, kx, ky, kz);
 }
 
 // Counters of a warp added to the instance's totals.
@@ -427,9 +439,7 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
 __device__ __forceinline__ void kick_of(const InstF32 &P, const Local &L, float srf, float &kx, float &ky,
                                         float &kz)
 {
-    kx = P.kick * (P.dc_scale * L.edx + srf * L.erx + L.esx);
-    ky = P.kick * (P.dc_scale * L.edy + srf * L.ery + L.esy);
-    kz = P.kick * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+    field_kick(L, P.kick, P.dc_scale, srf, kx, ky, kz);
 }
 
 // Collision-free tile: the U x blockDim.x packs of instance P starting at
@@ -780,9 +790,8 @@ __global__ void __launch_bounds__(256) dt_limits_kernel(GridF32 G, InstF32 P, Li
         if (L.nsig > 0.0f && L.T > 0.0f) lam = collision_rate(P, L, vx, vy, vz);
         vmax = sqrtf(vx * vx + vy * vy + vz * vz);
         const float srf = (float)A.srf;
-        const float ax = A.kick_m * (P.dc_scale * L.edx + srf * L.erx + L.esx);
-        const float ay = A.kick_m * (P.dc_scale * L.edy + srf * L.ery + L.esy);
-        const float az = A.kick_m * (P.dc_scale * L.edz + srf * L.erz + L.esz);
+        float ax, ay, az;
+        field_kick(L, A.kick_m, P.dc_scale, srf, ax, ay, az);
         const float am = sqrtf(ax * ax + ay * ay + az * az);
         const float vth = L.T > 0.0f ? sqrtf(A.kT_over_M_coef * L.T) : 0.0f;
         if (am > 0.0f) acc = 0.1f * fmaxf(vmax, vth) / am;
