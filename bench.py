@@ -47,7 +47,7 @@ def _peaks():
 class ClockSampler:
     """Samples of the SM clock and the clock-event (throttle) reasons during
     the timed region: NVML polled every 10 ms from a thread (read-only
-    queries), else nvidia-smi at its 200 ms period."""
+    queries), else nvidia-smi polled every 20 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -101,7 +101,7 @@ class ClockSampler:
             self.nvml_error = f"{type(e).__name__}: {e}"
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -163,7 +163,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline_run(n_packs=100_000, min_seconds=10.0, max_micro=4000, w=None):
+def cpu_baseline_run(n_packs=100_000, min_seconds=10.0, max_micro=20000, w=None):
     """The oracle as it stands on a bounded sample of the workload: the full
     pack count, advanced in chunks of 50 micro steps until at least
     `min_seconds` of CPU work (or `max_micro` micro steps) are done."""
@@ -242,9 +242,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=8)
     ap.add_argument("--serve-steps", type=int, default=100_000, help="micro steps per request (50 us)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-instances", type=int, default=64)
+    ap.add_argument("--sweep-steps", type=int, default=2000)
+    ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
-    ap.add_argument("--section", default="all", choices=["all", "fused", "streamed", "serving"],
+    ap.add_argument("--section", default="all", choices=["all", "fused", "streamed", "serving", "sweep"],
                     help="run only one timed section (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -259,6 +263,12 @@ def main():
         torch.cuda.set_device(local)
         build.build()
         print(json.dumps(_serving(args, local)))
+        return
+    if args.section == "sweep":
+        torch.cuda.set_device(local)
+        build.build()
+        dev = torch.device("cuda", local)
+        print(json.dumps(_sweep(args, local, torch.cuda.Stream(dev), dev)))
         return
     if args.section == "streamed":
         torch.cuda.set_device(local)
@@ -347,6 +357,9 @@ def main():
     streamed = None
     if not args.no_streamed:
         streamed = _streamed_push(args, local, stream, dev, peaks)
+    sweep = None
+    if not args.no_sweep:
+        sweep = _sweep(args, local, stream, dev)
     serve = None
     if not args.no_serving:
         serve = _serving(args, local)
@@ -364,6 +377,7 @@ def main():
                "gpu_launches": int(launches_step), "fp64_plain": fp64,
                "speedup_fp32_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
                "streamed_push": streamed,
+               "sweep": sweep,
                "serving": serve,
                "peaks_source": peak_src}
         print(json.dumps(out))
@@ -483,6 +497,47 @@ def _streamed_push(args, local, stream, dev, peaks):
             "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
             "note": "K=1 launches (graph replays of RF table + step + clock advance), no gas (push, gather, "
                     "classify), pool larger than L2"}
+
+
+def _sweep(args, local, stream, dev):
+    """Batched sweep (64 operating points of the ring stack: RF amplitude x DC
+    gradient x inlet pressure, pack counts log-uniform in [1e4, 5e5], seeds
+    100-163), each instance with its own 128 x 512 PIC grid updated every 10
+    micro steps, advanced together by graph-replayed macro steps in the
+    launch shape the autotuner picks."""
+    import dataclasses
+    import torch
+    from paper_2609_31258_b300 import mucite, workloads as W
+    g = W.Grid(512, 2048, 5e-3, 0.0, 40e-3)
+    pic = W.Grid(128, 512, 5e-3, 0.0, 40e-3)
+    f = W.ring_stack_fields(g, p_in=1000.0, pic=pic)
+    base = W.ring_stack(n_packs=1, n_steps=0)
+    pts = W.sweep_points(args.sweep_instances)
+    ctx = mucite.Context(local, stream)
+    ctx.load_fields(f)
+    for i, pt in enumerate(pts):
+        run = dataclasses.replace(base.run, v_rf=pt["v_rf"], dc_scale=pt["dc_scale"], p_scale=pt["p_scale"],
+                                  seed=pt["seed"], pic_interval=10)
+        ctx.inject(i, base.ion, dataclasses.replace(base.source, n_initial=pt["n_packs"]), run)
+    inst = list(range(len(pts)))
+    tuning = ctx.autotune(inst, args.sweep_tune_steps) if args.sweep_tune_steps > 0 else None
+    ctx.step(-1, 200)
+    torch.cuda.synchronize(dev)
+    p0 = sum(ctx.tally(i)["pack_steps"] for i in inst)
+    K = args.sweep_steps
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ctx.step(-1, K)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    ps = sum(ctx.tally(i)["pack_steps"] for i in inst) - p0
+    ctx.close()
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "instances": len(pts),
+            "packs": int(sum(pt["n_packs"] for pt in pts)), "micro_steps": K, "ms": ms,
+            "pic": "128x512 per instance, every 10 micro steps", "tuning": tuning,
+            "note": "macro step = batched PIC update of all instances + one fused launch of 10 micro steps, "
+                    "graph-replayed"}
 
 
 def _serving(args, local):

@@ -243,6 +243,32 @@ mucite_status mucite_step(mucite_ctx *ctx, int instance, int n_steps);
  * listed twice), MUCITE_E_STATE (an instance not injected), MUCITE_E_CUDA. */
 mucite_status mucite_step_set(mucite_ctx *ctx, const int *instances, int count, int n_steps);
 
+/* Launch shape chosen by mucite_autotune. */
+typedef struct {
+    int32_t steps_per_launch;         /* micro steps fused per launch (PIC runs: unchanged) */
+    int32_t threads_per_block;        /* packs per tile, as in mucite_set_tuning */
+    int32_t persistent_blocks_per_sm; /* as in mucite_set_launch_mode (0 = automatic) */
+    int32_t n_tried;                  /* shapes timed */
+    double best_ms_per_step;          /* device time of one micro step of the set, chosen shape */
+} mucite_tuning;
+
+/* Autotuner of the batched FP32 launch (no counterpart in the paper): times
+ * `trial_steps` micro steps of the listed instances (host array, each an
+ * injected FP32 instance, listed once) for every candidate shape -- packs
+ * per tile {64, 128, 256} x persistent blocks per SM {0, 1, 2, 3} x steps
+ * per launch {250, 500, 1000, 2000} up to trial_steps / 2 (with space
+ * charge on, the PIC interval fixes the steps per launch) -- each from the
+ * same saved state after an untimed pass of the same shape, then restores
+ * that state (pools, clocks, slot counts, source accumulators, counters,
+ * PIC charge, potential and field) and applies the fastest shape to the
+ * context. Takes a device copy of the listed pools (and PIC state) for the
+ * duration of the call. Synchronises the stream.
+ * Errors: MUCITE_E_ARG (bad list, FP64 instance, trial_steps outside
+ * [1, 100000]), MUCITE_E_STATE, MUCITE_E_OOM (no room for the copy),
+ * MUCITE_E_CUDA. */
+mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, int trial_steps,
+                              mucite_tuning *out);
+
 /* Space-charge macro step of one instance: int64 CIC deposit of q*W in units
  * of e * 2^-30 -> finite-volume cylindrical Poisson (dPhi/dr = 0 on the
  * axis, Phi = 0 at both axial ends and at r = R) solved by an FP32 DST-I in z

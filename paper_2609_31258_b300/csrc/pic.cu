@@ -29,12 +29,21 @@ namespace mucite {
 
 namespace {
 
+// floor(sqrt(v)) for v < 2^62, exact. An FP32 estimate (within ~2^-23
+// relative, i.e. below 2^8 for v < 2^62) refined by one Newton correction
+// from the exact integer residual v - r0^2 leaves r within 1 of the answer;
+// the integer tests settle it. FP32 keeps the deposit off the slow FP64 pipe.
 __device__ __forceinline__ uint64_t isqrt_floor(uint64_t v)
 {
-    uint64_t r = (uint64_t)sqrt((double)v);
-    while (r * r > v) --r;
-    while ((r + 1) * (r + 1) <= v) ++r;
-    return r;
+    if (v == 0) return 0;
+    const uint64_t r0 = (uint64_t)__fsqrt_rn((float)v);
+    const int64_t e = (int64_t)(v - r0 * r0); // |e| <= 2^9 r0 + 2^16, exact in 64 bits
+    int64_t r = (int64_t)r0 + (int64_t)__float2ll_rn((float)e / (2.0f * (float)r0));
+    if (r < 0) r = 0;
+    uint64_t u = (uint64_t)r;
+    while (u * u > v) --u;
+    while ((u + 1) * (u + 1) <= v) ++u;
+    return u;
 }
 
 __device__ __forceinline__ int32_t q32p(double v)
@@ -61,9 +70,13 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 } // namespace
 
-__device__ __forceinline__ void deposit_one(const DepositArgs &A, int64_t p)
+// Cell (j * pnr + i of its lower-left node) and the four CIC contributions
+// of pack p, in units of e * 2^-30; false when the pack deposits nothing
+// (inactive, or outside the PIC box).
+__device__ __forceinline__ bool deposit_weights(const DepositArgs &A, int64_t p, uint32_t &cell,
+                                                unsigned long long w[4])
 {
-    if (p >= A.n || A.status[p] != MUCITE_ACTIVE) return;
+    if (p >= A.n || A.status[p] != MUCITE_ACTIVE) return false;
     int32_t xq, yq, zq;
     if (A.precision == MUCITE_FP32) {
         xq = ((const int32_t *)A.x)[p];
@@ -76,7 +89,7 @@ __device__ __forceinline__ void deposit_one(const DepositArgs &A, int64_t p)
     }
     const uint64_t r2 = (uint64_t)((int64_t)xq * xq) + (uint64_t)((int64_t)yq * yq);
     const uint64_t r = isqrt_floor(r2);
-    if (r >= (1ULL << 30) || zq < 0 || zq > (1 << 30)) return;
+    if (r >= (1ULL << 30) || zq < 0 || zq > (1 << 30)) return false;
     const uint64_t tr = r * (uint64_t)(A.pnr - 1);
     const uint64_t tz = (uint64_t)zq * (uint64_t)(A.pnz - 1);
     int64_t i = (int64_t)(tr >> 30), j = (int64_t)(tz >> 30);
@@ -85,18 +98,35 @@ __device__ __forceinline__ void deposit_one(const DepositArgs &A, int64_t p)
     if (i > A.pnr - 2) { i = A.pnr - 2; fr = 1 << 15; }
     if (j > A.pnz - 2) { j = A.pnz - 2; fz = 1 << 15; }
     const int64_t wr0 = (1 << 15) - fr, wr1 = fr, wz0 = (1 << 15) - fz, wz1 = fz;
-    unsigned long long *Q = A.Q + (size_t)j * A.pnr + i;
-    atomicAdd(Q, (unsigned long long)(A.qw * wr0 * wz0));
-    atomicAdd(Q + 1, (unsigned long long)(A.qw * wr1 * wz0));
-    atomicAdd(Q + A.pnr, (unsigned long long)(A.qw * wr0 * wz1));
-    atomicAdd(Q + A.pnr + 1, (unsigned long long)(A.qw * wr1 * wz1));
+    cell = (uint32_t)(j * A.pnr + i);
+    w[0] = (unsigned long long)(A.qw * wr0 * wz0);
+    w[1] = (unsigned long long)(A.qw * wr1 * wz0);
+    w[2] = (unsigned long long)(A.qw * wr0 * wz1);
+    w[3] = (unsigned long long)(A.qw * wr1 * wz1);
+    return true;
 }
+
+// Charge deposit of one 256-pack tile. Packs of a beam crowd into few
+// cells, and atomics on one address serialise in L2; the block therefore
+// first sums its packs' contributions per cell in a shared-memory table
+// (open addressing on the cell index; the table has twice as many slots as
+// the block has packs, so every insertion finds a slot), then adds each
+// cell's four sums to the grid with one atomic per node. Integer addition
+// is exact and order-independent, so the result is bit-exact.
+constexpr int kDepBits = 9, kDepSlots = 1 << kDepBits;
+constexpr uint32_t kDepEmpty = 0xFFFFFFFFu;
 
 // Tile t of 256 packs belongs to instance i with tile_start[i] <= t < tile_start[i+1].
 __global__ void __launch_bounds__(256) deposit_kernel(const DepositArgs *args, const int32_t *tile_start,
                                                       int n_inst)
 {
     __shared__ int s_inst;
+    __shared__ uint32_t s_key[kDepSlots];
+    __shared__ unsigned long long s_acc[kDepSlots][4];
+    for (int k = threadIdx.x; k < kDepSlots; k += blockDim.x) {
+        s_key[k] = kDepEmpty;
+        s_acc[k][0] = s_acc[k][1] = s_acc[k][2] = s_acc[k][3] = 0ull;
+    }
     const int b = blockIdx.x;
     if (threadIdx.x == 0) {
         int lo = 0, hi = n_inst - 1;
@@ -108,8 +138,31 @@ __global__ void __launch_bounds__(256) deposit_kernel(const DepositArgs *args, c
         s_inst = lo;
     }
     __syncthreads();
-    const int inst = s_inst;
-    deposit_one(args[inst], (int64_t)(b - tile_start[inst]) * blockDim.x + threadIdx.x);
+    const DepositArgs &A = args[s_inst];
+    uint32_t cell;
+    unsigned long long w[4];
+    if (deposit_weights(A, (int64_t)(b - tile_start[s_inst]) * blockDim.x + threadIdx.x, cell, w)) {
+        uint32_t h = (cell * 2654435761u) >> (32 - kDepBits);
+        for (int probe = 0; probe < kDepSlots; ++probe) {
+            const uint32_t prev = atomicCAS(&s_key[h], kDepEmpty, cell);
+            if (prev == kDepEmpty || prev == cell) break;
+            h = (h + 1) & (kDepSlots - 1);
+        }
+        atomicAdd(&s_acc[h][0], w[0]);
+        atomicAdd(&s_acc[h][1], w[1]);
+        atomicAdd(&s_acc[h][2], w[2]);
+        atomicAdd(&s_acc[h][3], w[3]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kDepSlots; k += blockDim.x) {
+        const uint32_t c = s_key[k];
+        if (c == kDepEmpty) continue;
+        unsigned long long *Q = A.Q + c;
+        if (s_acc[k][0]) atomicAdd(Q, s_acc[k][0]);
+        if (s_acc[k][1]) atomicAdd(Q + 1, s_acc[k][1]);
+        if (s_acc[k][2]) atomicAdd(Q + A.pnr, s_acc[k][2]);
+        if (s_acc[k][3]) atomicAdd(Q + A.pnr + 1, s_acc[k][3]);
+    }
 }
 
 // Clears the node charges and the convergence bookkeeping of every instance

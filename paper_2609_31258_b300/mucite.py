@@ -22,7 +22,7 @@ MAX_INSTANCES = 256
 
 EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_fields",
            "mucite_state_layout", "mucite_inject", "mucite_release", "mucite_resume", "mucite_step",
-           "mucite_step_set",
+           "mucite_step_set", "mucite_autotune",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
            "mucite_dt_limits"]
@@ -71,6 +71,11 @@ class Layout(C.Structure):
                [("pos_bytes", C.c_int32), ("vel_bytes", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("steps_per_launch", C.c_int32), ("threads_per_block", C.c_int32),
+                ("persistent_blocks_per_sm", C.c_int32), ("n_tried", C.c_int32), ("best_ms_per_step", C.c_double)]
+
+
 _i64p = C.POINTER(C.c_int64)
 
 
@@ -107,6 +112,7 @@ def lib():
         L.mucite_resume.argtypes = [vp, C.c_int, C.c_int64, C.c_int64]
         L.mucite_step.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_step_set.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.c_int]
+        L.mucite_autotune.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(Tuning)]
         L.mucite_pic_update.argtypes = [vp, C.c_int]
         L.mucite_tally.argtypes = [vp, C.c_int, C.POINTER(TallyOut)]
         L.mucite_pic_read.argtypes = [vp, C.c_int, _i64p, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), dp]
@@ -234,6 +240,14 @@ class Context:
         """Advance the listed instances together (one batched launch per chunk)."""
         arr = (C.c_int * len(instances))(*[int(i) for i in instances])
         self._check(lib().mucite_step_set(self._p, arr, len(instances), int(n_steps)))
+
+    def autotune(self, instances, trial_steps):
+        """Time the candidate launch shapes on the listed instances (state
+        restored afterwards) and apply the fastest; returns the choice."""
+        arr = (C.c_int * len(instances))(*[int(i) for i in instances])
+        t = Tuning()
+        self._check(lib().mucite_autotune(self._p, arr, len(instances), int(trial_steps), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def pic_update(self, instance):
         self._check(lib().mucite_pic_update(self._p, instance))

@@ -117,3 +117,35 @@ def test_batched_space_charge(mc, graphs):
         assert (pic["Q"] == pref["Q"]).all()
         assert np.abs(pic["phi"] - pref["phi"]).max() <= 1e-12 * max(np.abs(pref["phi"]).max(), 1e-30)
     ctx.close()
+
+
+def test_autotune_restores_state_and_picks_a_shape(mc):
+    """The tuner times shapes on the live instances and restores them: the
+    run afterwards is bit-exact with an untuned run of the same instances."""
+    import torch
+    ws = [_ring(*p) for p in POINTS]
+    outs = []
+    for tune in (False, True):
+        ctx = mc.Context(0, torch.cuda.Stream())
+        ctx.set_tuning(64, 128)
+        ctx.load_fields(ws[0].fields)
+        for i, w in enumerate(ws):
+            ctx.inject(i, w.ion, w.source, w.run)
+        ctx.step(-1, 300)
+        if tune:
+            t = ctx.autotune([0, 1, 2], 600)
+            assert t["n_tried"] == 12 * 1 and t["best_ms_per_step"] > 0
+            assert t["threads_per_block"] in (64, 128, 256) and t["steps_per_launch"] == 250
+            with pytest.raises(mc.MuciteError):
+                ctx.autotune([0, 0], 10)
+        ctx.step(-1, 700)
+        outs.append(([download(ctx, i, w.source.n_initial) for i, w in enumerate(ws)],
+                     [ctx.tally(i) for i in range(3)]))
+        ctx.close()
+    (sa, ta), (sb, tb) = outs
+    for a, b in zip(sa, sb):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    for a, b in zip(ta, tb):
+        assert (a["count"] == b["count"]).all()
+        assert a["pack_steps"] == b["pack_steps"] and a["collisions"] == b["collisions"] and a["step"] == b["step"]
