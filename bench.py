@@ -243,12 +243,16 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=100_000, help="micro steps per request (50 us)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-pic", action="store_true")
+    ap.add_argument("--pic-packs", type=int, default=1_000_000)
+    ap.add_argument("--pic-steps", type=int, default=2000)
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
-    ap.add_argument("--section", default="all", choices=["all", "fused", "streamed", "serving", "sweep"],
+    ap.add_argument("--section", default="all",
+                    choices=["all", "fused", "streamed", "serving", "sweep", "space_charge"],
                     help="run only one timed section (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -263,6 +267,12 @@ def main():
         torch.cuda.set_device(local)
         build.build()
         print(json.dumps(_serving(args, local)))
+        return
+    if args.section == "space_charge":
+        torch.cuda.set_device(local)
+        build.build()
+        dev = torch.device("cuda", local)
+        print(json.dumps(_space_charge(args, local, torch.cuda.Stream(dev), dev)))
         return
     if args.section == "sweep":
         torch.cuda.set_device(local)
@@ -360,6 +370,9 @@ def main():
     sweep = None
     if not args.no_sweep:
         sweep = _sweep(args, local, stream, dev)
+    space_charge = None
+    if not args.no_pic:
+        space_charge = _space_charge(args, local, stream, dev)
     serve = None
     if not args.no_serving:
         serve = _serving(args, local)
@@ -378,6 +391,7 @@ def main():
                "speedup_fp32_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
                "streamed_push": streamed,
                "sweep": sweep,
+               "space_charge": space_charge,
                "serving": serve,
                "peaks_source": peak_src}
         print(json.dumps(out))
@@ -538,6 +552,44 @@ def _sweep(args, local, stream, dev):
             "pic": "128x512 per instance, every 10 micro steps", "tuning": tuning,
             "note": "macro step = batched PIC update of all instances + one fused launch of 10 micro steps, "
                     "graph-replayed"}
+
+
+def _space_charge(args, local, stream, dev):
+    """Cylinder with PIC space charge: 1e6 packs of 1 kDa/+1 (W = 1e3) in a
+    uniform axial field and 200 Pa N2, 256 x 1024 PIC grid updated every 10
+    micro steps (deposit, DST/tridiagonal solve with FP64 refinement to 1e-6,
+    E_SCE), continuous source; macro steps graph-replayed. The PIC share is
+    one minus the time of the same run without space charge over the time
+    with it."""
+    import dataclasses
+    import torch
+    from paper_2609_31258_b300 import mucite, workloads as W
+    w = W.cylinder_space_charge(n_packs=args.pic_packs, n_steps=0, precision=0)
+    K = args.pic_steps
+
+    def timed(run):
+        ctx = mucite.Context(local, stream)
+        ctx.load_fields(w.fields)
+        ctx.inject(0, w.ion, w.source, run, capacity=args.pic_packs + 100_000)
+        ctx.step(0, K)  # warm-up of the timed call's shape (graph capture)
+        torch.cuda.synchronize(dev)
+        T0 = ctx.tally(0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.step(0, K)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        T1 = ctx.tally(0)
+        rel = ctx.pic_read(0)["rel_residual"] if run.pic_interval else None
+        ctx.close()
+        return a.elapsed_time(b), T1["pack_steps"] - T0["pack_steps"], rel
+
+    ms, ps, rel = timed(w.run)
+    ms0, _, _ = timed(dataclasses.replace(w.run, pic_interval=0))
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "packs": args.pic_packs, "micro_steps": K, "ms": ms,
+            "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
+            "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
+            "last_rel_residual": rel, "pic_grid": "256x1024"}
 
 
 def _serving(args, local):

@@ -235,21 +235,25 @@ __global__ void check_kernel(const PicInst *insts, double tol)
 }
 
 // Tiled FP32 contraction C(m, n) = alpha * sum_k A(m, k) B(k, n) with strided
-// operands; 64 x 64 tile, 16-deep k slices, 4 x 4 outputs per thread.
-template <bool A_M_CONTIG, bool B_N_CONTIG>
+// operands; 64 x TN tile (TN = 64 or 32), 16-deep k slices, 4 x (TN / 16)
+// outputs per thread. The narrow tile doubles the blocks of a single-instance
+// transform (64 -> 128 on a 1022 x 255 problem) so that it covers the SMs.
+template <bool A_M_CONTIG, bool B_N_CONTIG, int TN>
 __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst *insts)
 {
+    constexpr int VN = TN / 16;          // outputs per thread along n
+    constexpr int LB = 16 * TN / 256;    // B elements loaded per thread per slice
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
     const float *A = g.a_is_S ? g.S : (g.a_sel == 0 ? I.r32 : I.hat);
     const float *B = g.b_is_S ? g.S : (g.b_sel == 0 ? I.r32 : I.hat);
     float *C = g.c_sel == 1 ? I.hat : I.d32;
     __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
+    __shared__ float Bs[16][TN + 4];
     const int tid = threadIdx.x;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * TN;
     const int tx = tid & 15, ty = tid >> 4;
-    float acc[4][4] = {};
+    float acc[4][VN] = {};
     for (int k0 = 0; k0 < g.K; k0 += 16) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -259,26 +263,28 @@ __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst 
             else { kk = e & 15; mm = e >> 4; }
             const int gm = m0 + mm, gk = k0 + kk;
             As[kk][mm] = (gm < g.Mo && gk < g.K) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
-            int nn;
-            if (B_N_CONTIG) { nn = e & 63; kk = e >> 6; }
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int e = tid + 256 * r;
+            int nn, kk;
+            if (B_N_CONTIG) { nn = e % TN; kk = e / TN; }
             else { kk = e & 15; nn = e >> 4; }
-            const int gn = n0 + nn;
-            const int gk2 = k0 + kk;
-            Bs[kk][nn] = (gn < g.No && gk2 < g.K) ? B[(size_t)gk2 * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < g.No && gk < g.K) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+            float a[4], b[VN];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = As[kk][ty * 4 + u];
-                b[u] = Bs[kk][tx * 4 + u];
-            }
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < VN; ++v) b[v] = Bs[kk][tx * VN + v];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+                for (int v = 0; v < VN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
         }
         __syncthreads();
     }
@@ -287,10 +293,57 @@ __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst 
         const int gm = m0 + ty * 4 + u;
         if (gm >= g.Mo) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int gn = n0 + tx * 4 + v;
+        for (int v = 0; v < VN; ++v) {
+            const int gn = n0 + tx * VN + v;
             if (gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * acc[u][v];
         }
+    }
+}
+
+// Tridiagonal solve per axial mode k, staged in shared memory: a block takes
+// kThModes consecutive modes, loads their right-hand sides and elimination
+// factors for all Nu <= kThRows radial rows with the whole block (coalesced
+// along k), runs the sequential forward and backward sweeps of one mode per
+// thread on shared memory, and writes the solution back. The sweeps are a
+// dependent chain of Nu steps, so their latency is that of shared memory,
+// not of L2; grids with more radial unknowns use thomas_kernel below.
+constexpr int kThModes = 16, kThRows = 256;
+
+__global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ float sh[kThRows][kThModes], sm[kThRows][kThModes], sc[kThRows][kThModes];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int k0 = blockIdx.x * kThModes;
+    const int n = G.Nu * kThModes;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = e / kThModes, kk = e % kThModes, k = k0 + kk;
+        if (k < G.M) {
+            const size_t o = (size_t)i * G.M + k;
+            sh[i][kk] = I.hat[o];
+            sm[i][kk] = G.invm[o];
+            sc[i][kk] = G.cp[o];
+        }
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < kThModes && k0 + t < G.M) {
+        float y = sh[0][t] * sm[0][t];
+        sh[0][t] = y;
+        for (int i = 1; i < G.Nu; ++i) {
+            y = (sh[i][t] - G.lo[i] * y) * sm[i][t];
+            sh[i][t] = y;
+        }
+        float x = y;
+        for (int i = G.Nu - 2; i >= 0; --i) {
+            x = sh[i][t] - sc[i][t] * x;
+            sh[i][t] = x;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = e / kThModes, kk = e % kThModes, k = k0 + kk;
+        if (k < G.M) I.hat[(size_t)i * G.M + k] = sh[i][kk];
     }
 }
 
@@ -378,11 +431,19 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
     inv.Mo = G.M; inv.No = G.Nu; inv.K = G.M;
     inv.a_sm = G.M; inv.a_sk = 1; inv.b_sk = 1; inv.b_sn = G.M; inv.c_sm = G.Nu; inv.c_sn = 1;
     inv.alpha = 1.0f;
-    const dim3 gf((G.M + 63) / 64, (G.Nu + 63) / 64, n_inst);
-    const dim3 gi((G.Nu + 63) / 64, (G.M + 63) / 64, n_inst);
-    dst_gemm_kernel<true, true><<<gf, 256, 0, s>>>(fwd, d_insts);
-    thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    dst_gemm_kernel<false, false><<<gi, 256, 0, s>>>(inv, d_insts);
+    // narrow tiles when the 64 x 64 grid would leave SMs idle
+    const bool narrow = (int64_t)((G.M + 63) / 64) * ((G.Nu + 63) / 64) * n_inst < 148;
+    const int tn = narrow ? 32 : 64;
+    const dim3 gf((G.M + tn - 1) / tn, (G.Nu + 63) / 64, n_inst);
+    const dim3 gi((G.Nu + tn - 1) / tn, (G.M + 63) / 64, n_inst);
+    if (narrow) dst_gemm_kernel<true, true, 32><<<gf, 256, 0, s>>>(fwd, d_insts);
+    else dst_gemm_kernel<true, true, 64><<<gf, 256, 0, s>>>(fwd, d_insts);
+    if (G.Nu <= kThRows)
+        thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    else
+        thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    if (narrow) dst_gemm_kernel<false, false, 32><<<gi, 256, 0, s>>>(inv, d_insts);
+    else dst_gemm_kernel<false, false, 64><<<gi, 256, 0, s>>>(inv, d_insts);
     return 3;
 }
 
