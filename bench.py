@@ -189,9 +189,10 @@ def cpu_baseline_run(n_packs=100_000, min_seconds=10.0, max_micro=20000, w=None)
 
 
 def _config(args, name, ws):
+    """The workload, identical for both arms (the launch shape is reported
+    separately by the CUDA arm)."""
     return {"workload": name, "grid": "512x2048", "packs_per_gpu": args.packs,
-            "micro_steps_per_step": args.micro, "steps_per_launch": args.spl or 2000,
-            "threads_per_block": args.threads or 256,
+            "micro_steps_per_step": args.micro,
             "l2": "flushed before every timed step (256 MiB write)",
             "parallelism": f"replicas x{ws}"}
 
@@ -231,6 +232,7 @@ def main():
     ap.add_argument("--packs", type=int, default=100_000)
     ap.add_argument("--spl", type=int, default=0, help="micro steps fused per launch (0 = tuned default)")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep 2000 steps per launch, 256-pack tiles")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -299,6 +301,11 @@ def main():
     ctx = mucite.Context(local, stream)
     ctx.set_tuning(args.spl or 2000, args.threads or 256)
     mucite.load_workload(ctx, w, 0)
+    tuning = None
+    if not args.spl and not args.threads and not args.no_autotune:
+        # the library's autotuner picks the launch shape (state restored after)
+        tuning = ctx.autotune([0], 2 * args.micro)
+        args.spl, args.threads = tuning["steps_per_launch"], tuning["threads_per_block"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def bench_step():
@@ -386,6 +393,8 @@ def main():
                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": _config(args, w.name, ws),
+               "launch": {"steps_per_launch": args.spl or 2000, "threads_per_block": args.threads or 256,
+                          "autotuned": tuning},
                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
                "gpu_launches": int(launches_step), "fp64_plain": fp64,
                "speedup_fp32_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
@@ -580,7 +589,8 @@ def _space_charge(args, local, stream, dev):
         b.record(stream)
         torch.cuda.synchronize(dev)
         T1 = ctx.tally(0)
-        rel = ctx.pic_read(0)["rel_residual"] if run.pic_interval else None
+        pr = ctx.pic_read(0) if run.pic_interval else {}
+        rel = (pr.get("rel_residual"), pr.get("iterations"))
         ctx.close()
         return a.elapsed_time(b), T1["pack_steps"] - T0["pack_steps"], rel
 
@@ -589,7 +599,7 @@ def _space_charge(args, local, stream, dev):
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "packs": args.pic_packs, "micro_steps": K, "ms": ms,
             "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
             "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
-            "last_rel_residual": rel, "pic_grid": "256x1024"}
+            "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024"}
 
 
 def _serving(args, local):

@@ -273,8 +273,10 @@ mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, 
  * of e * 2^-30 -> finite-volume cylindrical Poisson (dPhi/dr = 0 on the
  * axis, Phi = 0 at both axial ends and at r = R) solved by an FP32 DST-I in z
  * with a tridiagonal solve per mode, refined in FP64 until
- * ||b - A Phi|| / ||b|| <= 1e-6 (at most 8 refinements, warm-started from
- * the previous solution) -> E_SCE by central differences on the PIC grid.
+ * ||b - A Phi|| / ||b|| <= 1e-6 (at most 4 correction passes, warm-started
+ * from the previous solution; one or two suffice on the config workloads, and
+ * mucite_pic_read reports the residual reached and the passes taken) -> E_SCE
+ * by central differences on the PIC grid.
  * Errors: MUCITE_E_STATE (no PIC grid or instance), MUCITE_E_CUDA. */
 mucite_status mucite_pic_update(mucite_ctx *ctx, int instance);
 
@@ -285,10 +287,11 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
 
 /* Copy the instance's last space-charge solution to host buffers (any may be
  * NULL): Q int64 [pNz][pNr] (units e * 2^-30), phi FP64 [pNz][pNr],
- * E_r and E_z float [pNz][pNr], and the final relative residual.
- * Synchronises the stream. */
+ * E_r and E_z float [pNz][pNr], the final relative residual, and the number
+ * of correction passes (fast FP32 solves, or PCG iterations for the
+ * mask-aware solve) the last update took. Synchronises the stream. */
 mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double *phi, float *er,
-                              float *ez, double *rel_residual);
+                              float *ez, double *rel_residual, int32_t *iterations);
 
 /* Launch shape of the fused FP32 step: at most `steps_per_launch` micro
  * steps (1..6000) are fused per launch (state stays in registers between

@@ -133,6 +133,8 @@ template <typename T> void dfree(T *&p)
 
 int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
 
+constexpr int kPicRefine = 4; // FP32 correction passes of a plain space-charge solve
+
 void layout_of(int precision, int64_t cap, mucite_layout *L)
 {
     const int pb = precision == MUCITE_FP64 ? 8 : 4, vb = pb;
@@ -494,7 +496,9 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
     launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
     int64_t l = 2;
     const int n_plain = n_inst - n_masked;
-    if (n_plain > 0) l += launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, 8, 1e-6, ctx->stream);
+    // passes after convergence still launch (and return at once), so the cap
+    // is kept near what the warm-started solves need (one or two passes)
+    if (n_plain > 0) l += launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream);
     if (n_masked > 0) {
         PicGeom Gm = ctx->pg;
         Gm.metal = ctx->d_pic_metal;
@@ -1391,7 +1395,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
 }
 
 mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double *phi, float *er,
-                              float *ez, double *rel_residual)
+                              float *ez, double *rel_residual, int32_t *iterations)
 {
     const mucite_status st = check_instance(ctx, instance);
     if (st != MUCITE_OK) return st;
@@ -1414,6 +1418,7 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
         if (ez) ez[k] = e[k].y;
     }
     if (rel_residual) *rel_residual = red[2];
+    if (iterations) *iterations = (int32_t)red[3];
     return MUCITE_OK;
 }
 

@@ -235,58 +235,92 @@ __global__ void check_kernel(const PicInst *insts, double tol)
 }
 
 // Tiled FP32 contraction C(m, n) = alpha * sum_k A(m, k) B(k, n) with strided
-// operands; 64 x TN tile (TN = 64 or 32), 16-deep k slices, 4 x (TN / 16)
-// outputs per thread. The narrow tile doubles the blocks of a single-instance
-// transform (64 -> 128 on a 1022 x 255 problem) so that it covers the SMs.
+// operands; 64 x TN tile (TN = 64 or 32), 4 x (TN / 16) outputs per thread,
+// 32-deep k slices double-buffered in shared memory: while a slice is
+// multiplied, the next one is already on its way from L2 into registers, so
+// the L2 latency of the loads overlaps the arithmetic. The narrow tile
+// doubles the blocks of a single-instance transform (64 -> 128 on a
+// 1022 x 255 problem) so that it covers the SMs. The k order of every
+// output's sum is fixed, so results are deterministic.
 template <bool A_M_CONTIG, bool B_N_CONTIG, int TN>
 __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst *insts)
 {
+    constexpr int KS = 32;               // k slice depth
     constexpr int VN = TN / 16;          // outputs per thread along n
-    constexpr int LB = 16 * TN / 256;    // B elements loaded per thread per slice
+    constexpr int LA = 64 * KS / 256;    // A elements loaded per thread per slice
+    constexpr int LB = KS * TN / 256;    // B elements loaded per thread per slice
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
     const float *A = g.a_is_S ? g.S : (g.a_sel == 0 ? I.r32 : I.hat);
     const float *B = g.b_is_S ? g.S : (g.b_sel == 0 ? I.r32 : I.hat);
     float *C = g.c_sel == 1 ? I.hat : I.d32;
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][TN + 4];
+    __shared__ float As[2][KS][64 + 4];
+    __shared__ float Bs[2][KS][TN + 4];
     const int tid = threadIdx.x;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * TN;
     const int tx = tid & 15, ty = tid >> 4;
-    float acc[4][VN] = {};
-    for (int k0 = 0; k0 < g.K; k0 += 16) {
+    float ra[LA], rb[LB];
+    auto load = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < LA; ++r) {
             const int e = tid + 256 * r;
             int mm, kk;
             if (A_M_CONTIG) { mm = e & 63; kk = e >> 6; }
-            else { kk = e & 15; mm = e >> 4; }
+            else { kk = e % KS; mm = e / KS; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.Mo && gk < g.K) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
+            ra[r] = (gm < g.Mo && gk < g.K) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < LB; ++r) {
             const int e = tid + 256 * r;
             int nn, kk;
             if (B_N_CONTIG) { nn = e % TN; kk = e / TN; }
-            else { kk = e & 15; nn = e >> 4; }
+            else { kk = e % KS; nn = e / KS; }
             const int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < g.No && gk < g.K) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
+            rb[r] = (gn < g.No && gk < g.K) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
         }
-        __syncthreads();
+    };
+    auto store = [&](int buf) {
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
+        for (int r = 0; r < LA; ++r) {
+            const int e = tid + 256 * r;
+            int mm, kk;
+            if (A_M_CONTIG) { mm = e & 63; kk = e >> 6; }
+            else { kk = e % KS; mm = e / KS; }
+            As[buf][kk][mm] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int e = tid + 256 * r;
+            int nn, kk;
+            if (B_N_CONTIG) { nn = e % TN; kk = e / TN; }
+            else { kk = e % KS; nn = e / KS; }
+            Bs[buf][kk][nn] = rb[r];
+        }
+    };
+    float acc[4][VN] = {};
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < g.K; k0 += KS) {
+        const bool more = k0 + KS < g.K;
+        if (more) load(k0 + KS);
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
             float a[4], b[VN];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+            for (int u = 0; u < 4; ++u) a[u] = As[buf][kk][ty * 4 + u];
 #pragma unroll
-            for (int v = 0; v < VN; ++v) b[v] = Bs[kk][tx * VN + v];
+            for (int v = 0; v < VN; ++v) b[v] = Bs[buf][kk][tx * VN + v];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < VN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
         }
+        if (more) store(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {

@@ -115,7 +115,8 @@ def lib():
         L.mucite_autotune.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(Tuning)]
         L.mucite_pic_update.argtypes = [vp, C.c_int]
         L.mucite_tally.argtypes = [vp, C.c_int, C.POINTER(TallyOut)]
-        L.mucite_pic_read.argtypes = [vp, C.c_int, _i64p, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), dp]
+        L.mucite_pic_read.argtypes = [vp, C.c_int, _i64p, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), dp,
+                                      C.POINTER(C.c_int32)]
         L.mucite_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_set_launch_mode.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_launch_count.argtypes = [vp]
@@ -278,11 +279,12 @@ class Context:
         er = np.zeros(shape, np.float32)
         ez = np.zeros(shape, np.float32)
         rel = C.c_double()
+        its = C.c_int32()
         self._check(lib().mucite_pic_read(self._p, instance, Q.ctypes.data_as(_i64p),
                                           phi.ctypes.data_as(C.POINTER(C.c_double)),
                                           er.ctypes.data_as(C.POINTER(C.c_float)),
-                                          ez.ctypes.data_as(C.POINTER(C.c_float)), C.byref(rel)))
-        return dict(Q=Q, phi=phi, er=er, ez=ez, rel_residual=rel.value)
+                                          ez.ctypes.data_as(C.POINTER(C.c_float)), C.byref(rel), C.byref(its)))
+        return dict(Q=Q, phi=phi, er=er, ez=ez, rel_residual=rel.value, iterations=its.value)
 
     def set_tuning(self, steps_per_launch=0, threads_per_block=0):
         self._check(lib().mucite_set_tuning(self._p, int(steps_per_launch), int(threads_per_block)))
