@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
+    ap.add_argument("--serve-sustainable", type=int, default=-1,
+                    help="requests replayed at 70%% of capacity (-1: as many as --serve-requests, 0: skip)")
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
     ap.add_argument("--section", default="all",
@@ -613,10 +615,10 @@ def _serving(args, local):
     base = W.ring_stack(n_packs=1, n_steps=0, precision=0)
     t, n, tmpl = W.serving_arrivals(n_req=args.serve_requests, rate_hz=20.0, seed=5)
 
-    def once(rate):
+    def once(rate, count):
         arr = t * (20.0 / rate)
         reqs = [serving.make_request(i, arr[i], int(n[i]), W.SERVING_TEMPLATES[int(tmpl[i])], base,
-                                     n_steps=args.serve_steps, seed=1000 + i) for i in range(args.serve_requests)]
+                                     n_steps=args.serve_steps, seed=1000 + i) for i in range(count)]
         ctx = mucite.Context(local)
         ctx.set_tuning(2000, 256)
         ctx.load_fields(base.fields)
@@ -630,14 +632,14 @@ def _serving(args, local):
                 "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"], "mean_latency_s": lat.get("mean_s"),
                 "wall_s": wall, "pack_steps": int(work), "throughput": work / wall, "unit": UNIT}
 
-    first = once(20.0)
+    first = once(20.0, args.serve_requests)
     first.update({"micro_steps_per_request": args.serve_steps, "packs": [int(x) for x in n],
                   "templates": [int(x) for x in tmpl],
                   "note": "offered load exceeds capacity at 20 / s: latency is queue dominated"})
     busy = first["wall_s"] - float(t[0])
     capacity = len(n) / busy if busy > 0 else None
-    if capacity:
-        sus = once(0.7 * capacity)
+    if capacity and args.serve_sustainable != 0:
+        sus = once(0.7 * capacity, args.serve_sustainable if args.serve_sustainable > 0 else len(n))
         sus["note"] = "same requests, arrivals stretched to 70 % of the capacity measured at 20 / s"
         first["sustainable"] = sus
     return first
