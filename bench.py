@@ -256,7 +256,7 @@ def main():
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
     ap.add_argument("--section", default="all",
-                    choices=["all", "fused", "streamed", "serving", "sweep", "space_charge"],
+                    choices=["all", "fused", "streamed", "serving", "sweep", "space_charge", "paper_grid"],
                     help="run only one timed section (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -271,6 +271,12 @@ def main():
         torch.cuda.set_device(local)
         build.build()
         print(json.dumps(_serving(args, local)))
+        return
+    if args.section == "paper_grid":
+        torch.cuda.set_device(local)
+        build.build()
+        dev = torch.device("cuda", local)
+        print(json.dumps(_paper_grid(args, local, torch.cuda.Stream(dev), dev)))
         return
     if args.section == "space_charge":
         torch.cuda.set_device(local)
@@ -602,6 +608,35 @@ def _space_charge(args, local, stream, dev):
             "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
             "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
             "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024"}
+
+
+def _paper_grid(args, local, stream, dev):
+    """Fused FP32 step on a static grid of the paper's S-lens size (2001 x
+    6501 nodes, 468 MB of node records and mask: the gathers are served from
+    HBM through L2 rather than from an L2-resident table), 100,000 packs
+    filling the guide, 2000 micro steps per launch."""
+    import torch
+    from paper_2609_31258_b300 import mucite, workloads as W
+    w = W.paper_grid(n_packs=args.packs)
+    ctx = mucite.Context(local, stream)
+    ctx.set_tuning(2000, 256)
+    mucite.load_workload(ctx, w, 0)
+    for _ in range(2):
+        ctx.step(0, 2000)
+    torch.cuda.synchronize(dev)
+    T0 = ctx.tally(0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        ctx.step(0, 2000)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    T1 = ctx.tally(0)
+    ctx.close()
+    ms = a.elapsed_time(b)
+    ps = T1["pack_steps"] - T0["pack_steps"]
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "grid": "2001x6501", "packs": args.packs,
+            "micro_steps": 2000 * args.steps, "ms": ms, "collisions_per_pack_step": (T1["collisions"] - T0["collisions"]) / max(ps, 1)}
 
 
 def _serving(args, local):

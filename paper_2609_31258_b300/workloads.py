@@ -385,6 +385,34 @@ def cylinder_space_charge(n_packs=1_000_000, n_steps=200_000, seed=2, precision=
     return Workload(f"cylinder-pic-{pic_nr}x{pic_nz}-{n_packs}-packs", f, ION_1KDA, src, run, n_steps)
 
 
+def paper_grid(n_packs=100_000, seed=7, precision=0, nr=2001, nz=6501) -> Workload:
+    """Static grid of the paper's S-lens size (2001 x 6501 nodes at 0.01 mm,
+    r <= 20 mm, z in [0, 65] mm; 468 MB of FP32 node records and mask, not
+    L2-resident) with analytic fields in place of a Laplace solve: an RF
+    pattern alternating every 1.5 mm, (r / 4 mm)^2 cos(pi z / 1.5 mm), a DC
+    gradient of -2 V per 1.5 mm, no electrodes, and the free-jet gas of the
+    ring stack over 65 mm. Packs of 15 kDa/+8 fill the guide: prefilled
+    uniformly in z over [1, 64] mm, Gaussian in r with sigma = 1.5 mm
+    (truncated at 4.5 mm), Maxwellian at 300 K."""
+    g = Grid(nr, nz, 20e-3, 0.0, 65e-3)
+    r, z = node_coords(g)
+    zz, rr = np.meshgrid(z, r, indexing="ij")
+    phi_rf = (rr / 4e-3) ** 2 * np.cos(np.pi * zz / 1.5e-3)
+    phi_dc = -(2.0 / 1.5e-3) * zz
+    L = g.z1 - g.z0
+    gas_p = 1000.0 * np.power(0.1, zz / L)
+    gas_T = np.full_like(gas_p, 300.0)
+    gas_uz = 500.0 * (zz / L) * (1.0 - (rr / g.R) ** 2)
+    mask = np.zeros(phi_dc.shape, np.uint8)
+    f = Fields(g, phi_dc, phi_rf, gas_p, gas_T, np.zeros_like(gas_p), gas_uz, mask, np.full_like(gas_p, 1.0))
+    src = Source(profile=1, z_plane=0.0, radius=4.5e-3, sigma=1.5e-3, T_vel=300.0, half_space=0,
+                 n_initial=n_packs, prefill_z0=1e-3, prefill_z1=64e-3, weight=1)
+    run = Run(dt=0.5e-9, v_rf=100.0, f_rf=1e6, phi_rf=-math.pi / 2, dc_scale=1.0, p_scale=1.0, hit_dist=1e-5,
+              z_exit=65e-3, r_det=20e-3, seed=seed, precision=precision, exit_bin_steps=2000, n_exit_bins=40,
+              ke_max_ev=2.0, teff_max=1000.0)
+    return Workload(f"paper-grid-{nr}x{nz}-{n_packs}-packs", f, ION_15KDA, src, run, 0)
+
+
 def sweep_points(n_inst=64, seed_base=100, n_min=10_000, n_max=500_000):
     """Operating points of the batched sweep: a 4x4x4 grid of RF amplitude
     (100-300 Vpp), DC gradient (-0.5 to -4 V/ring) and inlet pressure
