@@ -283,7 +283,9 @@ def test_tally_bit_exact(mc, orc):
 # ---------------------------------------------------------------------------
 # Poisson solve
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("shape", [(65, 257), (256, 1024)])
+# (300, 129): more than 256 radial unknowns, the tridiagonal sweeps on global
+# memory; the others use the shared-memory staged sweeps
+@pytest.mark.parametrize("shape", [(65, 257), (256, 1024), (300, 129)])
 def test_poisson_matches_direct_solve(mc, orc, shape):
     from oracle import poisson
     pnr, pnz = shape
@@ -298,7 +300,7 @@ def test_poisson_matches_direct_solve(mc, orc, shape):
     Q = s.deposit()
     assert (got["Q"] == Q).all()
     ref = poisson.solve(w.fields.pic, Q)
-    assert got["rel_residual"] <= 1e-6
+    assert got["rel_residual"] <= 1e-6 and 1 <= got["iterations"] <= 4
     assert poisson.residual(w.fields.pic, Q, got["phi"]) <= 1e-6
     print("phi rel err", np.abs(got["phi"] - ref).max() / np.abs(ref).max(), "res", got["rel_residual"])
     assert np.abs(got["phi"] - ref).max() <= 1e-4 * np.abs(ref).max()
