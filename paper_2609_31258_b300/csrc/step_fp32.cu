@@ -202,6 +202,7 @@ __device__ __forceinline__ float u22(uint32_t hi, uint32_t lo)
 struct StepGas {
     float kx, ky, kz;          // velocity kick (q/m)(s_dc E_DC + s_rf(n) E_RF + E_SCE) dt
     float nsig, T, ux, uy, uz; // n sigma, gas temperature and flow
+    float s;                   // thermal speed sqrt(2 k_B T / m_gas)
 };
 
 // Collisions (Eq. 6): candidates form a Poisson process of rate
@@ -210,12 +211,13 @@ struct StepGas {
 // evaluation and draws nothing. One pass at time t of the step: the rest of
 // the step holds nu (dt - t) of optical depth; returns true when tau runs out
 // inside it (a candidate at t + tau / nu), else consumes that depth.
+// The relative speed w = |v - u| of the pass is returned for the candidate.
 __device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &S, float vx, float vy,
-                                               float vz, float &tau, float &t)
+                                               float vz, float &tau, float &t, float &w)
 {
-    const float cbar = 1.1283791670955126f * sqrt_fast(P.s_coef * S.T); // 2 s / sqrt(pi)
+    const float cbar = 1.1283791670955126f * S.s; // 2 s / sqrt(pi)
     const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
-    const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    w = sqrt_fast(wx * wx + wy * wy + wz * wz);
     const float nu = S.nsig * (w + cbar);
     const float room = nu * (P.dt - t);
     if (tau >= room) {
@@ -231,14 +233,14 @@ __device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &
 // magnitude, B.y and B.z partner direction, B.w and (A.x, A.y low bits)
 // scattering direction, (A.z, A.w) and (B.x, B.y) low bits the Beta uniforms,
 // (B.z, B.w) low bits the next optical depth. Returns 1 when accepted.
+// w: |v - u| from the pass of next_candidate that found the candidate.
 __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uint32_t pack, uint32_t step,
-                                         uint32_t kc, float &vx, float &vy, float &vz, float &eint,
+                                         uint32_t kc, float w, float &vx, float &vy, float &vz, float &eint,
                                          float &tau)
 {
-    const float s = sqrt_fast(P.s_coef * S.T);
+    const float s = S.s;
     const float cbar = 1.1283791670955126f * s;
     const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
-    const float w = sqrt_fast(wx * wx + wy * wy + wz * wz);
     uint4 A = make_uint4(pack, step, 2u * kc, 0u), B = make_uint4(pack, step, 2u * kc + 1u, 0u);
     philox10x2(A, B, P.key0, P.key1);
     tau = -__logf(u22(B.z, B.w));
@@ -531,7 +533,7 @@ template <bool kExtras>
 __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
                                            uint32_t pack, float fx, float fy, float rr, int32_t zq,
                                            float &vx, float &vy, float &vz, float &tau, float &t,
-                                           bool &lv, StepGas &S)
+                                           float &w, bool &lv, StepGas &S)
 {
     Local L;
     gather(G, P, fx, fy, rr, zq, L);
@@ -541,13 +543,14 @@ __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, c
     t = 0.0f;
     lv = false;
     if (!(S.nsig > 0.0f) || !(S.T > 0.0f)) return false;
+    S.s = sqrt_fast(P.s_coef * S.T);
     if (kExtras && P.langevin && zq >= P.lv_zq0 && zq <= P.lv_zq1)
         lv = collision_rate(P, S, vx, vy, vz) * P.dt >= P.lv_switch;
     if (lv) {
         langevin_step(P, S, pack, (uint32_t)(P.step0 + k), vx, vy, vz);
         return false;
     }
-    return next_candidate(P, S, vx, vy, vz, tau, t);
+    return next_candidate(P, S, vx, vy, vz, tau, t, w);
 }
 
 // Tile with collisions. Each lane owns a pack and walks through its steps;
@@ -580,10 +583,10 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
     float rr = lattice_r(fx, fy);
     unsigned n_coll = 0, n_ovf = 0;
     int k = 0, kc = 0, st = MUCITE_ACTIVE;
-    float t = 0.0f;
+    float t = 0.0f, w = 0.0f;
     bool lv = false, live = owned && nsteps > 0, pend = false;
     StepGas S;
-    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, lv, S);
+    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S);
     for (;;) {
         const bool can_push = live && !pend;
         const unsigned mc = __ballot_sync(0xffffffffu, pend);
@@ -591,13 +594,13 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         if ((mc | mp) == 0u) break;
         if (mc != 0u && __popc(mc) >= __popc(mp)) {
             if (pend) {
-                n_coll += (unsigned)candidate(P, S, pack, (uint32_t)(P.step0 + k), (uint32_t)kc, vx, vy, vz,
-                                              eint, tau);
+                n_coll += (unsigned)candidate(P, S, pack, (uint32_t)(P.step0 + k), (uint32_t)kc, w, vx, vy,
+                                              vz, eint, tau);
                 if (++kc == kKmax) {
                     ++n_ovf; // candidate cap: the rest of the step holds no further candidate
                     pend = false;
                 } else {
-                    pend = next_candidate(P, S, vx, vy, vz, tau, t);
+                    pend = next_candidate(P, S, vx, vy, vz, tau, t, w);
                 }
             }
         } else if (can_push) {
@@ -615,7 +618,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
             if (st != MUCITE_ACTIVE || k == nsteps)
                 live = false;
             else
-                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, lv, S);
+                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S);
         }
     }
     if (owned) {
