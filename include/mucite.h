@@ -127,7 +127,8 @@ typedef struct {
     /* pic_masked != 0: the space-charge solve also imposes Phi = 0 on metal
      * nodes of the PIC grid (the electrode mask at the nearest static node),
      * by conjugate gradients preconditioned with the maskless fast solve
-     * (at most 200 iterations, same 1e-6 tolerance). */
+     * (at most 100 iterations, same 1e-6 tolerance; mucite_pic_read reports
+     * the iterations taken and the residual reached). */
     int32_t pic_masked;
     /* integrator 0: leapfrog (kick-drift, one field evaluation per step);
      * 1: fourth-order Runge-Kutta under the instantaneous total field (the

@@ -134,6 +134,10 @@ template <typename T> void dfree(T *&p)
 int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
 
 constexpr int kPicRefine = 4; // FP32 correction passes of a plain space-charge solve
+// PCG iterations of a mask-aware solve: 13-59 were needed on the ring stack
+// (PIC 65 x 257 and 256 x 1024, cold and warm starts); iterations after
+// convergence still cost their launches, so the cap stays near that
+constexpr int kPcgIter = 100;
 
 void layout_of(int precision, int64_t cap, mucite_layout *L)
 {
@@ -502,7 +506,7 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
     if (n_masked > 0) {
         PicGeom Gm = ctx->pg;
         Gm.metal = ctx->d_pic_metal;
-        l += launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, 200, 1e-6, ctx->stream);
+        l += launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, kPcgIter, 1e-6, ctx->stream);
         launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
         l += 1;
     }

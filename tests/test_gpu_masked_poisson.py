@@ -34,7 +34,7 @@ def test_masked_poisson_matches_direct(orc, pic_shape):
     metal = poisson.pic_metal_from_static(w.fields.grid, w.fields.mask, w.fields.pic)
     assert metal.any() and (~metal).any()
     ref = poisson.solve_masked(w.fields.pic, Q, metal)
-    assert got["rel_residual"] <= 1e-6
+    assert got["rel_residual"] <= 1e-6 and got["iterations"] < 100
     assert poisson.residual_masked(w.fields.pic, Q, got["phi"], metal) <= 2e-6
     assert (got["phi"][metal] == 0.0).all()
     assert np.abs(got["phi"] - ref).max() <= 1e-4 * np.abs(ref).max()
