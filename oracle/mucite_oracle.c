@@ -563,7 +563,9 @@ void orc_run_steps(const orc_fields *F, const orc_ion *ion, const orc_run *run, 
             if (ion->dH_kJmol > 0.0 && !lv)
                 lnsy -= orc_eyring_rate(ion, orc_T_of_eint(ion, eint)) * run->dt;
             if (run->integrator == 1) {
-                /* RK4 under the instantaneous total field (L38, L108): four field
+                /* RK4 under the instantaneous total field (Methods, "Simulation scope and
+                 * modular architecture" and "Particle transport, collisions, and
+                 * effective internal temperature"): four field
                  * evaluations at t_n, t_n + dt/2 (twice) and t_n + dt */
                 double h = run->dt, sh = orc_rf_scalar_half(run, n), s1 = orc_rf_scalar(run, n + 1);
                 double p[3] = {x, y, z}, a1[3], a2[3], a3[3], a4[3], v2[3], v3[3], v4[3], q[3];

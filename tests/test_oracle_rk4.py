@@ -1,5 +1,6 @@
-"""Pins of the oracle's RK4 pusher (L38, L108), of dt segments and of the
-Eq. 1 micro-step limits.
+"""Pins of the oracle's RK4 pusher (Methods, "Particle transport, collisions,
+and effective internal temperature"), of dt segments and of the Eq. 1
+micro-step limits.
 
 - constant force: RK4 positions and velocities are exact (cubic and higher
   terms vanish);
