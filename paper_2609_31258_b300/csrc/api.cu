@@ -47,6 +47,7 @@ struct Instance {
 struct mucite_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr; // captures the bodies of device-controlled solve loops
     std::string err;
     bool fields = false;
     mucite_grid g{};
@@ -204,6 +205,8 @@ void free_instance(Instance &I)
     dfree(I.pic.z64);
     dfree(I.pic.q64);
     dfree(I.pic.p64);
+    dfree(I.pic.part);
+    dfree(I.pic.ticket);
     I = Instance();
 }
 
@@ -493,22 +496,30 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in,
 }
 
 // Space-charge macro step of a group: clear, deposit, solve, E_SCE -- a fixed
-// number of launches for any number of instances.
+// number of launches for any number of instances. Issued directly, passes
+// after convergence still launch (and return at once), so the caps are kept
+// near what the warm-started solves need; under graph capture the solve loops
+// become device-controlled while nodes that stop at convergence. Returns the
+// launches issued, or -1 when a captured loop could not be built.
 int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
 {
     launch_pic_prepare(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
     launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
     int64_t l = 2;
     const int n_plain = n_inst - n_masked;
-    // passes after convergence still launch (and return at once), so the cap
-    // is kept near what the warm-started solves need (one or two passes)
-    if (n_plain > 0) l += launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream);
+    if (n_plain > 0) {
+        const int k = launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream, ctx->aux);
+        if (k < 0) return -1;
+        l += k;
+    }
     if (n_masked > 0) {
         PicGeom Gm = ctx->pg;
         Gm.metal = ctx->d_pic_metal;
-        l += launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, kPcgIter, 1e-6, ctx->stream);
+        const int k =
+            launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, kPcgIter, 1e-6, ctx->stream, ctx->aux);
+        if (k < 0) return -1;
         launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
-        l += 1;
+        l += k + 1;
     }
     return l;
 }
@@ -519,7 +530,9 @@ mucite_status pic_update_group(mucite_ctx *ctx, const std::vector<Instance *> &g
     int total = 0, nm = 0;
     const mucite_status st = pic_upload(ctx, grp, total, nm);
     if (st != MUCITE_OK) return st;
-    ctx->launches += pic_launch(ctx, (int)grp.size(), total, nm);
+    const int64_t l = pic_launch(ctx, (int)grp.size(), total, nm);
+    if (l < 0) return fail(ctx, MUCITE_E_CUDA, "capture of the solve loop failed");
+    ctx->launches += l;
     CKL();
     return MUCITE_OK;
 }
@@ -649,11 +662,17 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                 int64_t l = 0;
-                if (P0 > 0) l += pic_launch(ctx, (int)n, ptiles, pmasked);
+                const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked) : 0;
+                l += lp;
                 l += step_launch(ctx, grp, tiles, chunk);
                 launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
                 l += 1;
                 const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+                if (ce == cudaSuccess && lp < 0) {
+                    cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    return fail(ctx, MUCITE_E_CUDA, "graph capture of the solve loop failed");
+                }
                 if (ce != cudaSuccess) return fail(ctx, MUCITE_E_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
                 const cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
                 cudaGraphDestroy(g);
@@ -741,6 +760,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_limits, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         fail(nullptr, MUCITE_E_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
         dfree(ctx->d_insts);
@@ -749,6 +769,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
         dfree(ctx->d_dep);
         dfree(ctx->d_dep_tiles);
         dfree(ctx->d_limits);
+        if (ctx->aux) cudaStreamDestroy(ctx->aux);
         delete ctx;
         return MUCITE_E_OOM;
     }
@@ -772,6 +793,7 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_rf);
     dfree(ctx->d_limits);
     drop_graph(ctx);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
 }
 
@@ -1005,6 +1027,9 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
             CK(cudaMalloc(&I.pic.q64, nu * sizeof(double)));
             CK(cudaMalloc(&I.pic.p64, nn * sizeof(double)));
             CK(cudaMemsetAsync(I.pic.p64, 0, nn * sizeof(double), ctx->stream));
+            CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
+            CK(cudaMalloc(&I.pic.ticket, sizeof(unsigned)));
+            CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         }
         if (run->precision == MUCITE_FP64) {
             CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));

@@ -487,14 +487,56 @@ void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream
     esc_kernel<<<dim3((unsigned)std::min<int64_t>((nn + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(G, d_insts);
 }
 
-int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
+__global__ void loop_reset_kernel(const PicInst *insts)
+{
+    if (threadIdx.x == 0) insts[0].red[7] = 0.0;
+}
+
+__global__ void loop_ctl_kernel(const PicInst *insts, int n_inst, int max_passes, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    const double c = insts[0].red[7] + 1.0;
+    insts[0].red[7] = c;
+    bool open = false;
+    for (int i = 0; i < n_inst; ++i) open = open || *insts[i].conv == 0;
+    cudaGraphSetConditional(h, (open && c < (double)max_passes) ? 1u : 0u);
+}
+
+void launch_loop_reset(const PicInst *d_insts, cudaStream_t s)
+{
+    loop_reset_kernel<<<1, 32, 0, s>>>(d_insts);
+}
+
+void launch_loop_ctl(const PicInst *d_insts, int n_inst, int max_passes, cudaGraphConditionalHandle h,
                      cudaStream_t s)
+{
+    loop_ctl_kernel<<<1, 32, 0, s>>>(d_insts, n_inst, max_passes, h);
+}
+
+int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
+                     cudaStream_t s, cudaStream_t aux)
 {
     int launches = 0;
     const int64_t nu = (int64_t)G.M * G.Nu;
     const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
     bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
     ++launches;
+    // graph capture: initial residual, then at most max_refine passes of
+    // (fast solve, update, residual, check) under device control
+    if (max_refine > 0 && stream_capturing(s, aux)) {
+        residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);
+        const bool looped = capture_while(s, aux, d_insts, [&](cudaStream_t b, cudaGraphConditionalHandle h) {
+            launch_fast_solve(G, d_insts, n_inst, b);
+            update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
+            residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
+            check_kernel<<<n_inst, 32, 0, b>>>(d_insts, tol);
+            launch_loop_ctl(d_insts, n_inst, max_refine, h, b);
+        });
+        if (!looped) return -1;
+        launch_esc(G, d_insts, n_inst, s);
+        return launches + 4;
+    }
     for (int it = 0; it <= max_refine; ++it) {
         residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
         check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);

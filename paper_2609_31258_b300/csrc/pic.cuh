@@ -1,7 +1,7 @@
 // Device-side descriptors of the space-charge solve (see pic.cu).
 #pragma once
-
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -29,11 +29,17 @@ struct PicInst {
     float *d32;              // [M][Nu] correction
     float2 *esc;             // [pnz][pnr] (E_r, E_z)
     double *er64, *ez64;     // FP64 copies for the FP64 path (or NULL)
-    double *red;             // [0] ||b||^2, [1] ||r||^2, [2] rel. residual, [3] iterations, [4..6] PCG scalars
+    double *red;             // [0] ||b||^2, [1] ||r||^2, [2] rel. residual, [3] iterations, [4..6] PCG scalars,
+                             // [7] pass counter of a captured solve loop (first instance of a launch)
     int *conv;               // converged flag
     double *r64, *z64, *q64; // [M][Nu] PCG vectors (mask-aware solve) or NULL
     double *p64;             // [pnz][pnr] PCG search direction or NULL
+    double *part;            // [2][kRedBlocks] per-block partial sums of the mask-aware solve or NULL
+    unsigned *ticket;        // arrival counter of those partial sums (zero between launches) or NULL
 };
+
+// Most blocks a solve kernel launches per instance (8 per SM on 148 SMs).
+constexpr int kRedBlocks = 1184;
 
 struct DepositArgs {
     int precision;
@@ -59,14 +65,71 @@ struct DstGemm {
 void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,
                     cudaStream_t s);
 void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
-// Returns the number of kernel launches issued.
+// Returns the number of kernel launches issued. When `s` is being captured
+// into a CUDA graph and `aux` is a stream of this device, the correction
+// passes become the body of a device-controlled while loop (a conditional
+// graph node, its body captured on `aux`), so a replay runs only the passes
+// the solve needs instead of the fixed maximum; otherwise the passes are
+// issued as a fixed sequence whose kernels return at once after convergence.
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
-                     cudaStream_t s);
+                     cudaStream_t s, cudaStream_t aux = nullptr);
 // Maskless fast solve A d = r: r32 -> (DST-I, Thomas per mode, inverse DST-I) -> d32.
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 // Mask-aware solve by PCG preconditioned with the fast solve (pic_masked.cu).
 int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_iter, double tol,
-                            cudaStream_t s);
+                            cudaStream_t s, cudaStream_t aux = nullptr);
+
+// Device-controlled loop for a stream under capture: adds a while node after
+// the captured work of `s`, captures `body(aux)` as its body and lets the
+// capture of `s` continue after the node. The body must end with
+// launch_loop_ctl. Returns false when `s` is not being captured, `aux` is
+// null or a graph call fails (the capture is then unusable).
+template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body);
+// Loop control of a captured while node: counts the passes (kept in the
+// first instance's red[7], cleared by launch_loop_reset before the node) and
+// continues while a listed instance is unconverged and fewer than max_passes
+// passes have run.
+void launch_loop_reset(const PicInst *d_insts, cudaStream_t s);
+void launch_loop_ctl(const PicInst *d_insts, int n_inst, int max_passes, cudaGraphConditionalHandle h,
+                     cudaStream_t s);
+
+inline bool stream_capturing(cudaStream_t s, cudaStream_t aux)
+{
+    if (aux == nullptr) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+
+template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body)
+{
+    if (!stream_capturing(s, aux)) return false;
+    launch_loop_reset(d_insts, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return false;
+    const std::vector<cudaGraphNode_t> dep(deps, deps + nd);
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) return false;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddNode(&node, g, dep.data(), nullptr, dep.size(), &p) != cudaSuccess) return false;
+    cudaGraph_t bg = p.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(aux, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return false;
+    body(aux, h);
+    cudaGraph_t done = nullptr;
+    if (cudaStreamEndCapture(aux, &done) != cudaSuccess) return false;
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+           cudaSuccess;
+}
 // E_SCE by central differences of Phi.
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 

@@ -35,6 +35,38 @@ __device__ __forceinline__ double block_sum_m(double v, double *sh)
     return v;
 }
 
+// Order-independent grid sum of one instance: every block stores its partial
+// sums, and the last block to arrive adds all of them in block order and
+// writes the totals to red[s0] (and red[s1]), so the result, and with it
+// every PCG scalar, does not depend on the order in which blocks finish.
+// Called by all threads of a block with its partials v0 (and v1) in thread 0.
+__device__ void grid_sum(const PicInst &I, double v0, double v1, bool two, int s0, int s1, double *sh)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        I.part[blockIdx.x] = v0;
+        if (two) I.part[kRedBlocks + blockIdx.x] = v1;
+        __threadfence();
+        last = atomicAdd(I.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+        a += __ldcg(I.part + k);
+        if (two) b += __ldcg(I.part + kRedBlocks + k);
+    }
+    a = block_sum_m(a, sh);
+    __syncthreads();
+    if (two) b = block_sum_m(b, sh);
+    if (threadIdx.x == 0) {
+        I.red[s0] = a;
+        if (two) I.red[s1] = b;
+        *I.ticket = 0u;
+    }
+}
+
 // (A x)_ij on an unknown node for a full-grid vector x (zero on the Dirichlet
 // boundary and, for the vectors used here, on metal nodes).
 __device__ __forceinline__ double apply_A(const PicGeom &G, const double *x, int i, int j)
@@ -75,10 +107,7 @@ __global__ void __launch_bounds__(256) pcg_init_kernel(PicGeom G, const PicInst 
     bb = block_sum_m(bb, sh);
     __syncthreads();
     rr = block_sum_m(rr, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(&I.red[kBB], bb);
-        atomicAdd(&I.red[kRR], rr);
-    }
+    grid_sum(I, bb, rr, true, kBB, kRR, sh);
 }
 
 // z = P A^-1 P r from the fast solve's output d32; rz = r . z.
@@ -97,7 +126,7 @@ __global__ void __launch_bounds__(256) pcg_z_kernel(PicGeom G, const PicInst *in
         rz += I.r64[e] * z;
     }
     rz = block_sum_m(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(&I.red[kRZN], rz);
+    grid_sum(I, rz, 0.0, false, kRZN, kRZN, sh);
 }
 
 // beta = rz_new / rz (0 on the first iteration), p = z + beta p (full grid).
@@ -131,7 +160,7 @@ __global__ void __launch_bounds__(256) pcg_q_kernel(PicGeom G, const PicInst *in
         pq += I.p64[(size_t)j * G.pnr + i] * q;
     }
     pq = block_sum_m(pq, sh);
-    if (threadIdx.x == 0) atomicAdd(&I.red[kPQ], pq);
+    grid_sum(I, pq, 0.0, false, kPQ, kPQ, sh);
 }
 
 // alpha = rz / pq; Phi += alpha p; r -= alpha q; ||r||^2.
@@ -154,7 +183,7 @@ __global__ void __launch_bounds__(256) pcg_xr_kernel(PicGeom G, const PicInst *i
         rr += r * r;
     }
     rr = block_sum_m(rr, sh);
-    if (threadIdx.x == 0) atomicAdd(&I.red[kRR], rr);
+    grid_sum(I, rr, 0.0, false, kRR, kRR, sh);
 }
 
 // One thread per instance: rel = ||r|| / ||b|| after the initial residual
@@ -183,11 +212,11 @@ __global__ void pcg_rotate_kernel(const PicInst *insts)
 }
 
 int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_iter, double tol,
-                            cudaStream_t s)
+                            cudaStream_t s, cudaStream_t aux)
 {
     int launches = 0;
     const int64_t nu = (int64_t)G.M * G.Nu;
-    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
+    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, kRedBlocks);
     const dim3 gv(blocks, 1, n_inst);
     pcg_init_kernel<<<gv, 256, 0, s>>>(G, d_insts);
     pcg_scalar_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol, 0);
@@ -198,6 +227,24 @@ int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst
     pcg_p_kernel<<<gv, 256, 0, s>>>(G, d_insts, 1);
     pcg_rotate_kernel<<<n_inst, 32, 0, s>>>(d_insts);
     launches += 3;
+    // graph capture: the first (q, x/r, scalars) step, then at most
+    // max_iter - 1 further iterations under device control
+    if (max_iter > 1 && stream_capturing(s, aux)) {
+        pcg_q_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+        pcg_xr_kernel<<<gv, 256, 0, s>>>(G, d_insts);
+        pcg_scalar_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol, 2);
+        const bool looped = capture_while(s, aux, d_insts, [&](cudaStream_t b, cudaGraphConditionalHandle h) {
+            launch_fast_solve(G, d_insts, n_inst, b);
+            pcg_z_kernel<<<gv, 256, 0, b>>>(G, d_insts);
+            pcg_p_kernel<<<gv, 256, 0, b>>>(G, d_insts, 0);
+            pcg_rotate_kernel<<<n_inst, 32, 0, b>>>(d_insts);
+            pcg_q_kernel<<<gv, 256, 0, b>>>(G, d_insts);
+            pcg_xr_kernel<<<gv, 256, 0, b>>>(G, d_insts);
+            pcg_scalar_kernel<<<n_inst, 32, 0, b>>>(d_insts, tol, 2);
+            launch_loop_ctl(d_insts, n_inst, max_iter - 1, h, b);
+        });
+        return looped ? launches + 5 : -1;
+    }
     for (int it = 0; it < max_iter; ++it) {
         pcg_q_kernel<<<gv, 256, 0, s>>>(G, d_insts);
         pcg_xr_kernel<<<gv, 256, 0, s>>>(G, d_insts);
