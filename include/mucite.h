@@ -69,8 +69,9 @@ typedef struct {
     double R, z0, z1;
 } mucite_grid;
 
-/* Ion template (Methods, "Simulation scope": mass, charge state, collision
- * cross section, atom count, heat-capacity profile). Heat capacity
+/* Ion template (Methods, "Simulation scope": the species is described by its
+ * mass, its charge, its cross section for collisions with the gas, the number
+ * of its atoms and how its heat capacity varies with T). Heat capacity
  * Cv / k_B = 3 n_atoms * min(1, cv_c0 + cv_c1 * T); classical: (1, 0). */
 typedef struct {
     double mass_da;
@@ -79,8 +80,8 @@ typedef struct {
     double n_atoms;
     double cv_c0, cv_c1;
     double T_init; /* initial T_eff */
-    /* Transition-state parameters of the dissociation model (Eq. 7,
-     * "Dissociation is modeled as a temperature dependent loss"): activation
+    /* Transition-state parameters of the dissociation model (Eq. 7, a loss
+     * rate that depends on T_eff): activation
      * enthalpy [kJ/mol] and entropy [J/(mol K)]; dH_kJmol <= 0 disables it.
      * Every micro step, after the collisions, ln SY -= k(T_eff) dt with the
      * Eyring rate k = (k_B T/h) exp(dS/R) exp(-dH/(R T)). */
@@ -115,7 +116,8 @@ typedef struct {
     int32_t pic_interval; /* steps between space-charge updates, 0 = none */
     int32_t exit_bin_steps, n_exit_bins, n_r_bins, n_ke_bins, n_teff_bins, n_loss_r, n_loss_z;
     double ke_max_ev, teff_max;
-    /* Hybrid Langevin branch (Methods, "optional hybrid Langevin branch";
+    /* Hybrid Langevin branch (Methods, Particle transport, collisions, and
+     * effective internal temperature: the optional lumped-relaxation mode;
      * Table S2: switch at lambda dt >= 0.05): with langevin != 0, a pack in
      * z in [lv_z0, lv_z1] whose expected collision rate satisfies
      * lambda dt >= lv_switch gets an exact Ornstein-Uhlenbeck update of its

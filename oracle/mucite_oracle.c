@@ -189,8 +189,8 @@ double orc_eyring_rate(const orc_ion *ion, double T)
 }
 
 /* ------------------------------------------------------------------------- */
-/* E from a potential by central differences (field bake, "Electric fields   */
-/* are obtained from the baked potentials"): E = -grad(phi), interior central,*/
+/* E from a potential by central differences (field bake; the paper takes E  */
+/* from the baked potentials): E = -grad(phi), interior central,              */
 /* one-sided at the domain edges, E_r = 0 on the axis.                        */
 /* ------------------------------------------------------------------------- */
 void orc_efield_from_phi(int nr, int nz, double dr, double dz, const double *phi, double *er,
@@ -424,9 +424,10 @@ double orc_collision_rate(const orc_ion *ion, const orc_run *run, const orc_loca
     return L->n * ion->ccs_m2 * gbar;
 }
 
-/* Hybrid Langevin branch ("optional hybrid Langevin branch ... aggregated
- * velocity relaxation toward the local gas velocity plus a temperature
- * dependent stochastic component"): exact Ornstein-Uhlenbeck update of the
+/* Hybrid Langevin branch (Methods, Particle transport, collisions, and
+ * effective internal temperature: an optional mode that relaxes the velocity
+ * toward the gas flow in one lumped step, with a random part set by the gas
+ * temperature): exact Ornstein-Uhlenbeck update of the
  * velocity relative to the flow over dt,
  *   v <- u + (v - u) e^{-gamma dt} + sqrt(kT/M (1 - e^{-2 gamma dt})) xi,
  * with the friction gamma = q / (M K) from the low-field Mason-Schamp

@@ -2,9 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Follows "Axisymmetric PIC space charge update": the Poisson operator is
-written in finite-volume form over annular control volumes around each node
-of the (r, z) PIC grid; dPhi/dr = 0 at r = 0 (no flux through the axis);
+Follows "Axisymmetric PIC space charge update": the Poisson operator is a
+finite-volume balance on the ring-shaped cell that surrounds each node of
+the (r, z) PIC grid; dPhi/dr = 0 at r = 0 (no flux through the axis);
 Phi = 0 at both axial ends and at the outer radius. Metal-mask nodes are not
 imposed (the workloads with space charge have no electrodes inside the PIC
 domain). The right-hand side is the node charge Q deposited by CIC, so the

@@ -1,9 +1,9 @@
 // Field loading on the device: E = -grad(phi) by central differences of the
-// baked potentials ("Electric fields are obtained from the baked
-// potentials"; the paper's spline derivative is read as second-order central
-// differences, one-sided at the domain edges, E_r = 0 on the symmetry axis),
-// then packing of the FP32 node records and the FP32 mask/distance field
-// ("Gas field and electrode mask coupling").
+// baked potentials (the paper derives E from the baked potentials; its
+// spline derivative is read as second-order central differences, one-sided
+// at the domain edges, E_r = 0 on the symmetry axis), then packing of the
+// FP32 node records and the FP32 mask/distance field ("Gas field and
+// electrode mask coupling").
 #include "common.cuh"
 
 namespace mucite {

@@ -1,5 +1,6 @@
-// Mask-aware space-charge solve ("Zero perturbation potential is imposed at
-// the axial boundaries, the outer radial boundary, and metal mask nodes").
+// Mask-aware space-charge solve (Methods, Axisymmetric PIC space charge
+// update: the space-charge potential vanishes at both axial ends, at the
+// outer radius and on the metal nodes of the electrode mask).
 //
 // A direct DST/tridiagonal solve cannot impose Phi = 0 at interior metal
 // nodes, so the masked system A_m Phi = b_m (metal rows replaced by the
