@@ -867,6 +867,7 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
     if (pic) {
         PicGeom &G = ctx->pg;
         G = PicGeom{};
+        G.n_sm = ctx->sm_count;
         G.pnr = pic->nr;
         G.pnz = pic->nz;
         G.M = pic->nz - 2;

@@ -22,6 +22,8 @@
 // 4. E_SCE = -grad(Phi) by central differences on the PIC grid (one-sided at
 //    the edges, E_r = 0 on the axis).
 // blockIdx.z selects the instance in batched launches.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "pic.cuh"
 
@@ -235,49 +237,53 @@ __global__ void check_kernel(const PicInst *insts, double tol)
 }
 
 // Tiled FP32 contraction C(m, n) = alpha * sum_k A(m, k) B(k, n) with strided
-// operands; 64 x TN tile (TN = 64 or 32), 4 x (TN / 16) outputs per thread,
-// 32-deep k slices double-buffered in shared memory: while a slice is
-// multiplied, the next one is already on its way from L2 into registers, so
-// the L2 latency of the loads overlaps the arithmetic. The narrow tile
-// doubles the blocks of a single-instance transform (64 -> 128 on a
-// 1022 x 255 problem) so that it covers the SMs. The k order of every
-// output's sum is fixed, so results are deterministic.
-template <bool A_M_CONTIG, bool B_N_CONTIG, int TN>
-__global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst *insts)
+// operands. A CTA computes a 64 x 64 output tile, 4 x 4 outputs per thread,
+// over 32-deep k slices double-buffered in shared memory: while a slice is
+// multiplied, the next one is already on its way from L2 into registers.
+// Small problems split the k range over the CTAs of a thread-block cluster
+// (`splits` CTAs along x, cluster rank = split): each CTA leaves its partial
+// tile in its shared memory and, after a cluster barrier, CTA r adds the
+// partials of its share of the rows through distributed shared memory in
+// rank order. Every output's sum has a fixed order, so results are
+// deterministic.
+template <bool A_M_CONTIG, bool B_N_CONTIG>
+__global__ void __launch_bounds__(256, 2) dst_gemm_kernel(DstGemm g, const PicInst *insts, int splits)
 {
-    constexpr int KS = 32;               // k slice depth
-    constexpr int VN = TN / 16;          // outputs per thread along n
-    constexpr int LA = 64 * KS / 256;    // A elements loaded per thread per slice
-    constexpr int LB = KS * TN / 256;    // B elements loaded per thread per slice
+    constexpr int KS = 32, BM = 64, BN = 64, PAD = 4;
+    constexpr int LA = BM * KS / 256, LB = KS * BN / 256;
     const PicInst &I = insts[blockIdx.z];
-    if (*I.conv) return;
+    if (*I.conv) return; // uniform over a cluster: its CTAs share blockIdx.z
     const float *A = g.a_is_S ? g.S : (g.a_sel == 0 ? I.r32 : I.hat);
     const float *B = g.b_is_S ? g.S : (g.b_sel == 0 ? I.r32 : I.hat);
     float *C = g.c_sel == 1 ? I.hat : I.d32;
-    __shared__ float As[2][KS][64 + 4];
-    __shared__ float Bs[2][KS][TN + 4];
+    __shared__ __align__(16) float smem[2 * KS * (BM + PAD) + 2 * KS * (BN + PAD)];
+    float(*As)[KS][BM + PAD] = reinterpret_cast<float(*)[KS][BM + PAD]>(smem);
+    float(*Bs)[KS][BN + PAD] = reinterpret_cast<float(*)[KS][BN + PAD]>(smem + 2 * KS * (BM + PAD));
     const int tid = threadIdx.x;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * TN;
+    const int split = (int)(blockIdx.x % (unsigned)splits);
+    const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x / (unsigned)splits) * BN;
     const int tx = tid & 15, ty = tid >> 4;
+    const int nsl = (g.K + KS - 1) / KS, per = (nsl + splits - 1) / splits;
+    const int kb = split * per * KS, ke = min(g.K, (split + 1) * per * KS);
     float ra[LA], rb[LB];
     auto load = [&](int k0) {
 #pragma unroll
         for (int r = 0; r < LA; ++r) {
             const int e = tid + 256 * r;
             int mm, kk;
-            if (A_M_CONTIG) { mm = e & 63; kk = e >> 6; }
+            if (A_M_CONTIG) { mm = e & (BM - 1); kk = e / BM; }
             else { kk = e % KS; mm = e / KS; }
             const int gm = m0 + mm, gk = k0 + kk;
-            ra[r] = (gm < g.Mo && gk < g.K) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
+            ra[r] = (gm < g.Mo && gk < ke) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < LB; ++r) {
             const int e = tid + 256 * r;
             int nn, kk;
-            if (B_N_CONTIG) { nn = e % TN; kk = e / TN; }
+            if (B_N_CONTIG) { nn = e & (BN - 1); kk = e / BN; }
             else { kk = e % KS; nn = e / KS; }
             const int gn = n0 + nn, gk = k0 + kk;
-            rb[r] = (gn < g.No && gk < g.K) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
+            rb[r] = (gn < g.No && gk < ke) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
         }
     };
     auto store = [&](int buf) {
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst 
         for (int r = 0; r < LA; ++r) {
             const int e = tid + 256 * r;
             int mm, kk;
-            if (A_M_CONTIG) { mm = e & 63; kk = e >> 6; }
+            if (A_M_CONTIG) { mm = e & (BM - 1); kk = e / BM; }
             else { kk = e % KS; mm = e / KS; }
             As[buf][kk][mm] = ra[r];
         }
@@ -293,45 +299,70 @@ __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst 
         for (int r = 0; r < LB; ++r) {
             const int e = tid + 256 * r;
             int nn, kk;
-            if (B_N_CONTIG) { nn = e % TN; kk = e / TN; }
+            if (B_N_CONTIG) { nn = e & (BN - 1); kk = e / BN; }
             else { kk = e % KS; nn = e / KS; }
             Bs[buf][kk][nn] = rb[r];
         }
     };
-    float acc[4][VN] = {};
-    load(0);
-    store(0);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < g.K; k0 += KS) {
-        const bool more = k0 + KS < g.K;
-        if (more) load(k0 + KS);
-#pragma unroll
-        for (int kk = 0; kk < KS; ++kk) {
-            float a[4], b[VN];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = As[buf][kk][ty * 4 + u];
-#pragma unroll
-            for (int v = 0; v < VN; ++v) b[v] = Bs[buf][kk][tx * VN + v];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < VN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-        }
-        if (more) store(buf ^ 1);
+    float acc[4][4] = {};
+    if (kb < ke) {
+        load(kb);
+        store(0);
         __syncthreads();
-        buf ^= 1;
-    }
+        int buf = 0;
+        for (int k0 = kb; k0 < ke; k0 += KS) {
+            const bool more = k0 + KS < ke;
+            if (more) load(k0 + KS);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int gm = m0 + ty * 4 + u;
-        if (gm >= g.Mo) continue;
+            for (int kk = 0; kk < KS; ++kk) {
+                const float4 a = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+                const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int v = 0; v < VN; ++v) {
-            const int gn = n0 + tx * VN + v;
-            if (gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * acc[u][v];
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+            }
+            if (more) store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
         }
     }
+    if (splits == 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int gm = m0 + ty * 4 + u;
+            if (gm >= g.Mo) continue;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int gn = n0 + tx * 4 + v;
+                if (gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * acc[u][v];
+            }
+        }
+        return;
+    }
+    // split-K: partial tile to shared memory (the slice buffers are free after
+    // the loop's last barrier), rank-ordered sum over the cluster
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    float(*Ps)[BN + PAD] = reinterpret_cast<float(*)[BN + PAD]>(smem);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Ps[ty * 4 + u][tx * 4 + v] = acc[u][v];
+    cluster.sync();
+    const int rows = BM / splits, r0 = split * rows;
+    for (int e = tid; e < rows * BN; e += 256) {
+        const int rr = r0 + e / BN, cc = e % BN;
+        float sum = 0.0f;
+        for (int q = 0; q < splits; ++q) {
+            const float *rp = cluster.map_shared_rank(&Ps[0][0], (unsigned)q);
+            sum += rp[rr * (BN + PAD) + cc];
+        }
+        const int gm = m0 + rr, gn = n0 + cc;
+        if (gm < g.Mo && gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * sum;
+    }
+    cluster.sync(); // partials stay readable until every CTA of the cluster is done
 }
 
 // Tridiagonal solve per axial mode k, staged in shared memory: a block takes
@@ -339,17 +370,21 @@ __global__ void __launch_bounds__(256) dst_gemm_kernel(DstGemm g, const PicInst 
 // factors for all Nu <= kThRows radial rows with the whole block (coalesced
 // along k), runs the sequential forward and backward sweeps of one mode per
 // thread on shared memory, and writes the solution back. The sweeps are a
-// dependent chain of Nu steps, so their latency is that of shared memory,
-// not of L2; grids with more radial unknowns use thomas_kernel below.
-constexpr int kThModes = 16, kThRows = 256;
+// dependent chain of Nu steps; the operands of the next 8 rows are fetched
+// into registers while the current 8 are eliminated, so a step costs the
+// chain's arithmetic rather than a shared-memory round trip. Grids with more
+// radial unknowns use thomas_kernel below.
+constexpr int kThModes = 8, kThRows = 256;
 
 __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicInst *insts)
 {
-    __shared__ float sh[kThRows][kThModes], sm[kThRows][kThModes], sc[kThRows][kThModes];
+    constexpr int U = 8;
+    __shared__ float sh[kThRows][kThModes], sm[kThRows][kThModes], sc[kThRows][kThModes], sl[kThRows];
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
     const int k0 = blockIdx.x * kThModes;
-    const int n = G.Nu * kThModes;
+    const int Nu = G.Nu;
+    const int n = Nu * kThModes;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int i = e / kThModes, kk = e % kThModes, k = k0 + kk;
         if (k < G.M) {
@@ -359,19 +394,75 @@ __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicIn
             sc[i][kk] = G.cp[o];
         }
     }
+    for (int i = threadIdx.x; i < Nu; i += blockDim.x) sl[i] = G.lo[i];
     __syncthreads();
     const int t = threadIdx.x;
     if (t < kThModes && k0 + t < G.M) {
-        float y = sh[0][t] * sm[0][t];
-        sh[0][t] = y;
-        for (int i = 1; i < G.Nu; ++i) {
-            y = (sh[i][t] - G.lo[i] * y) * sm[i][t];
-            sh[i][t] = y;
+        // forward: y_0 = h_0 / m_0, y_i = (h_i - a_i y_{i-1}) / m_i
+        float ch[U], cm[U], cl[U], nh[U], nm[U], nl[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = u < Nu;
+            ch[u] = ok ? sh[u][t] : 0.0f;
+            cm[u] = ok ? sm[u][t] : 0.0f;
+            cl[u] = ok && u > 0 ? sl[u] : 0.0f; // row 0 has no sub-diagonal term
         }
+        float y = 0.0f;
+        for (int i0 = 0; i0 < Nu; i0 += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + U + u;
+                const bool ok = i < Nu;
+                nh[u] = ok ? sh[i][t] : 0.0f;
+                nm[u] = ok ? sm[i][t] : 0.0f;
+                nl[u] = ok ? sl[i] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u;
+                if (i < Nu) {
+                    y = (ch[u] - cl[u] * y) * cm[u];
+                    sh[i][t] = y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                ch[u] = nh[u];
+                cm[u] = nm[u];
+                cl[u] = nl[u];
+            }
+        }
+        // backward: x_{Nu-1} = y_{Nu-1}, x_i = y_i - (c_i / m_i) x_{i+1}
         float x = y;
-        for (int i = G.Nu - 2; i >= 0; --i) {
-            x = sh[i][t] - sc[i][t] * x;
-            sh[i][t] = x;
+        float cy[U], cc[U], ny[U], nc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = Nu - 2 - u;
+            const bool ok = i >= 0;
+            cy[u] = ok ? sh[i][t] : 0.0f;
+            cc[u] = ok ? sc[i][t] : 0.0f;
+        }
+        for (int i1 = Nu - 2; i1 >= 0; i1 -= U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i1 - U - u;
+                const bool ok = i >= 0;
+                ny[u] = ok ? sh[i][t] : 0.0f;
+                nc[u] = ok ? sc[i][t] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i1 - u;
+                if (i >= 0) {
+                    x = cy[u] - cc[u] * x;
+                    sh[i][t] = x;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cy[u] = ny[u];
+                cc[u] = nc[u];
+            }
         }
     }
     __syncthreads();
@@ -452,6 +543,25 @@ void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int 
     deposit_kernel<<<total_tiles, 256, 0, s>>>(d_args, d_tile_start, n_inst);
 }
 
+// Launch of a contraction with `splits` CTAs per cluster along x.
+void launch_gemm(void (*kern)(DstGemm, const PicInst *, int), dim3 grid, int splits, const DstGemm &g,
+                 const PicInst *d_insts, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)splits;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, g, d_insts, splits);
+}
+
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
     DstGemm fwd{}, inv{};
@@ -465,19 +575,20 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
     inv.Mo = G.M; inv.No = G.Nu; inv.K = G.M;
     inv.a_sm = G.M; inv.a_sk = 1; inv.b_sk = 1; inv.b_sn = G.M; inv.c_sm = G.Nu; inv.c_sn = 1;
     inv.alpha = 1.0f;
-    // narrow tiles when the 64 x 64 grid would leave SMs idle
-    const bool narrow = (int64_t)((G.M + 63) / 64) * ((G.Nu + 63) / 64) * n_inst < 148;
-    const int tn = narrow ? 32 : 64;
-    const dim3 gf((G.M + tn - 1) / tn, (G.Nu + 63) / 64, n_inst);
-    const dim3 gi((G.Nu + tn - 1) / tn, (G.M + 63) / 64, n_inst);
-    if (narrow) dst_gemm_kernel<true, true, 32><<<gf, 256, 0, s>>>(fwd, d_insts);
-    else dst_gemm_kernel<true, true, 64><<<gf, 256, 0, s>>>(fwd, d_insts);
+    // split the k range over a cluster of 2 or 4 CTAs while the 64 x 64
+    // tiles would leave the SMs without a second resident CTA
+    const int sms = G.n_sm > 0 ? G.n_sm : 148;
+    const int64_t tiles = (int64_t)((G.M + 63) / 64) * ((G.Nu + 63) / 64) * n_inst;
+    int splits = 1;
+    while (splits < 4 && tiles * splits < 2 * sms && (G.M + 31) / 32 >= 4 * splits) splits *= 2;
+    const dim3 gf((unsigned)(((G.M + 63) / 64) * splits), (G.Nu + 63) / 64, n_inst);
+    const dim3 gi((unsigned)(((G.Nu + 63) / 64) * splits), (G.M + 63) / 64, n_inst);
+    launch_gemm(dst_gemm_kernel<true, true>, gf, splits, fwd, d_insts, s);
     if (G.Nu <= kThRows)
         thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
     else
         thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    if (narrow) dst_gemm_kernel<false, false, 32><<<gi, 256, 0, s>>>(inv, d_insts);
-    else dst_gemm_kernel<false, false, 64><<<gi, 256, 0, s>>>(inv, d_insts);
+    launch_gemm(dst_gemm_kernel<false, false>, gi, splits, inv, d_insts, s);
     return 3;
 }
 

@@ -18,6 +18,7 @@ struct PicGeom {
     const float *lo;         // [Nu] a_i (sub-diagonal)
     const double *a, *c, *A; // [Nu] FP64 operator coefficients
     const uint8_t *metal;    // [pnz][pnr] metal nodes (mask-aware solve) or NULL
+    int n_sm;                // SMs of the device (0: 148), sizes the split of small contractions
 };
 
 // Per-instance buffers of the space-charge solve.
