@@ -1028,10 +1028,10 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
             CK(cudaMalloc(&I.pic.q64, nu * sizeof(double)));
             CK(cudaMalloc(&I.pic.p64, nn * sizeof(double)));
             CK(cudaMemsetAsync(I.pic.p64, 0, nn * sizeof(double), ctx->stream));
-            CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
             CK(cudaMalloc(&I.pic.ticket, sizeof(unsigned)));
             CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         }
+        CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
         if (run->precision == MUCITE_FP64) {
             CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));
             CK(cudaMalloc(&I.pic.ez64, nn * sizeof(double)));

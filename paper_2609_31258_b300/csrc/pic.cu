@@ -194,7 +194,10 @@ __global__ void __launch_bounds__(256) bnorm_kernel(PicGeom G, const PicInst *in
         acc += b * b;
     }
     acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) atomicAdd(&I.red[0], acc);
+    if (threadIdx.x == 0) {
+        if (I.part) I.part[kRedBlocks + blockIdx.x] = acc; // added up in block order by check_kernel
+        else atomicAdd(&I.red[0], acc);
+    }
 }
 
 // r = b - A Phi (FP64) on the unknowns; r32 = (float) r; ||r||^2 into red[1].
@@ -220,14 +223,35 @@ __global__ void __launch_bounds__(256) residual_kernel(PicGeom G, const PicInst 
         acc += r * r;
     }
     acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) atomicAdd(&I.red[1], acc);
+    if (threadIdx.x == 0) {
+        if (I.part) I.part[blockIdx.x] = acc; // added up in block order by check_kernel
+        else atomicAdd(&I.red[1], acc);
+    }
 }
 
-// Convergence decision: red[2] = ||r|| / ||b||; conv when <= tol.
-__global__ void check_kernel(const PicInst *insts, double tol)
+// Convergence decision: red[2] = ||r|| / ||b||; conv when <= tol. With
+// per-block partial sums (I.part), ||r||^2 (and, on the first check of a
+// solve, ||b||^2) are first added up over the nblk blocks in block order, so
+// the decision does not depend on the order in which the blocks finished.
+__global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double tol, int nblk, int first)
 {
+    __shared__ double sh[32];
     const PicInst &I = insts[blockIdx.x];
-    if (threadIdx.x != 0 || *I.conv) return;
+    if (*I.conv) return;
+    if (I.part) {
+        double a = 0.0;
+        for (int k = threadIdx.x; k < nblk; k += blockDim.x) a += I.part[k];
+        a = block_sum(a, sh);
+        if (threadIdx.x == 0) I.red[1] = a;
+        if (first) {
+            __syncthreads();
+            double b = 0.0;
+            for (int k = threadIdx.x; k < nblk; k += blockDim.x) b += I.part[kRedBlocks + k];
+            b = block_sum(b, sh);
+            if (threadIdx.x == 0) I.red[0] = b;
+        }
+    }
+    if (threadIdx.x != 0) return;
     const double bb = I.red[0], rr = I.red[1];
     const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     I.red[2] = rel;
@@ -508,6 +532,17 @@ __global__ void __launch_bounds__(256) update_kernel(PicGeom G, const PicInst *i
 
 __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *insts)
 {
+    // FP64 division is slow on this part: the four step reciprocals are
+    // formed once per block and the differences multiplied by them
+    __shared__ double rcp[4];
+    if (threadIdx.x == 0) {
+        rcp[0] = 1.0 / G.dr;
+        rcp[1] = 1.0 / (2.0 * G.dr);
+        rcp[2] = 1.0 / G.dz;
+        rcp[3] = 1.0 / (2.0 * G.dz);
+    }
+    __syncthreads();
+    const double idr = rcp[0], i2dr = rcp[1], idz = rcp[2], i2dz = rcp[3];
     const PicInst &I = insts[blockIdx.z];
     const int64_t n = (int64_t)G.pnr * G.pnz;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -516,11 +551,11 @@ __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *inst
         const double *ph = I.phi + e;
         double dpr, dpz;
         if (i == 0) dpr = 0.0;
-        else if (i == G.pnr - 1) dpr = (ph[0] - ph[-1]) / G.dr;
-        else dpr = (ph[1] - ph[-1]) / (2.0 * G.dr);
-        if (j == 0) dpz = (ph[G.pnr] - ph[0]) / G.dz;
-        else if (j == G.pnz - 1) dpz = (ph[0] - ph[-G.pnr]) / G.dz;
-        else dpz = (ph[G.pnr] - ph[-G.pnr]) / (2.0 * G.dz);
+        else if (i == G.pnr - 1) dpr = (ph[0] - ph[-1]) * idr;
+        else dpr = (ph[1] - ph[-1]) * i2dr;
+        if (j == 0) dpz = (ph[G.pnr] - ph[0]) * idz;
+        else if (j == G.pnz - 1) dpz = (ph[0] - ph[-G.pnr]) * idz;
+        else dpz = (ph[G.pnr] - ph[-G.pnr]) * i2dz;
         I.esc[e] = make_float2((float)-dpr, (float)-dpz);
         if (I.er64) {
             I.er64[e] = -dpr;
@@ -636,12 +671,12 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
     // (fast solve, update, residual, check) under device control
     if (max_refine > 0 && stream_capturing(s, aux)) {
         residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);
+        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, (int)blocks, 1);
         const bool looped = capture_while(s, aux, d_insts, [&](cudaStream_t b, cudaGraphConditionalHandle h) {
             launch_fast_solve(G, d_insts, n_inst, b);
             update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
             residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
-            check_kernel<<<n_inst, 32, 0, b>>>(d_insts, tol);
+            check_kernel<<<n_inst, 256, 0, b>>>(d_insts, tol, (int)blocks, 0);
             launch_loop_ctl(d_insts, n_inst, max_refine, h, b);
         });
         if (!looped) return -1;
@@ -650,7 +685,7 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
     }
     for (int it = 0; it <= max_refine; ++it) {
         residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        check_kernel<<<n_inst, 32, 0, s>>>(d_insts, tol);
+        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, (int)blocks, it == 0 ? 1 : 0);
         launches += 2;
         if (it == max_refine) break;
         launches += launch_fast_solve(G, d_insts, n_inst, s);

@@ -35,7 +35,7 @@ struct PicInst {
     int *conv;               // converged flag
     double *r64, *z64, *q64; // [M][Nu] PCG vectors (mask-aware solve) or NULL
     double *p64;             // [pnz][pnr] PCG search direction or NULL
-    double *part;            // [2][kRedBlocks] per-block partial sums of the mask-aware solve or NULL
+    double *part;            // [2][kRedBlocks] per-block partial sums (block-ordered reductions) or NULL
     unsigned *ticket;        // arrival counter of those partial sums (zero between launches) or NULL
 };
 

@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(256) pcg_p_kernel(PicGeom G, const PicInst *in
 {
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
-    const double beta = first ? 0.0 : I.red[kRZN] / I.red[kRZ];
+    __shared__ double sb;
+    if (threadIdx.x == 0) sb = first ? 0.0 : I.red[kRZN] / I.red[kRZ]; // one FP64 division per block
+    __syncthreads();
+    const double beta = sb;
     const int64_t n = (int64_t)G.M * G.Nu;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -170,7 +173,10 @@ __global__ void __launch_bounds__(256) pcg_xr_kernel(PicGeom G, const PicInst *i
     __shared__ double sh[32];
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
-    const double alpha = I.red[kRZ] / I.red[kPQ];
+    __shared__ double sa;
+    if (threadIdx.x == 0) sa = I.red[kRZ] / I.red[kPQ]; // one FP64 division per block
+    __syncthreads();
+    const double alpha = sa;
     const int64_t n = (int64_t)G.M * G.Nu;
     double rr = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
