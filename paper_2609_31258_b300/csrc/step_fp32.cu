@@ -648,7 +648,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
 constexpr int kFreeU = 2;
 
 template <bool kCollide, bool kExtras>
-__global__ void __launch_bounds__(kCollide ? 256 : 128, kCollide ? 3 : 6)
+__global__ void __launch_bounds__(kCollide ? 256 : 128, kCollide ? 4 : 6)
     step_f32_kernel(GridF32 G, const InstF32 *insts,
                                                        const int32_t *tile_start, int n_inst,
                                                        int total_tiles, int nsteps)
