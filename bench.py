@@ -252,6 +252,10 @@ def main():
     ap.add_argument("--no-pic", action="store_true")
     ap.add_argument("--pic-packs", type=int, default=1_000_000)
     ap.add_argument("--pic-steps", type=int, default=2000)
+    ap.add_argument("--pic-direct", action="store_true",
+                    help="space-charge section without graph replay: the solves run their fixed pass "
+                         "sequence as separate launches (a profiler cannot see the kernels of graphs "
+                         "that hold device-controlled loops)")
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
@@ -590,6 +594,8 @@ def _space_charge(args, local, stream, dev):
 
     def timed(run):
         ctx = mucite.Context(local, stream)
+        if args.pic_direct:
+            ctx.set_launch_mode(0, False)
         ctx.load_fields(w.fields)
         ctx.inject(0, w.ion, w.source, run, capacity=args.pic_packs + 100_000)
         ctx.step(0, K)  # warm-up of the timed call's shape (graph capture)
@@ -611,7 +617,8 @@ def _space_charge(args, local, stream, dev):
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "packs": args.pic_packs, "micro_steps": K, "ms": ms,
             "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
             "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
-            "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024"}
+            "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024",
+            "launch": "direct (fixed solve passes)" if args.pic_direct else "graph-replayed macro steps"}
 
 
 def _paper_grid(args, local, stream, dev):

@@ -284,8 +284,11 @@ def test_tally_bit_exact(mc, orc):
 # Poisson solve
 # ---------------------------------------------------------------------------
 # (300, 129): more than 256 radial unknowns, the tridiagonal sweeps on global
-# memory; the others use the shared-memory staged sweeps
-@pytest.mark.parametrize("shape", [(65, 257), (256, 1024), (300, 129)])
+# memory; the others use the shared-memory staged sweeps. (3, 5) and (7, 4):
+# fewer unknowns than one tile or one batch of the sweeps' row prefetch;
+# (33, 65): one ragged tile, k range not split; (65, 257) and (300, 129): k
+# range split over clusters of 2 CTAs; (256, 1024): over clusters of 4.
+@pytest.mark.parametrize("shape", [(65, 257), (256, 1024), (300, 129), (3, 5), (7, 4), (33, 65)])
 def test_poisson_matches_direct_solve(mc, orc, shape):
     from oracle import poisson
     pnr, pnz = shape
