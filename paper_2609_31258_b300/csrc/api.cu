@@ -48,6 +48,7 @@ struct mucite_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr; // captures the bodies of device-controlled solve loops
+    bool device_loops = true;   // cleared if a driver cannot build them: fixed pass sequences instead
     std::string err;
     bool fields = false;
     mucite_grid g{};
@@ -508,7 +509,8 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
     int64_t l = 2;
     const int n_plain = n_inst - n_masked;
     if (n_plain > 0) {
-        const int k = launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream, ctx->aux);
+        const int k = launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream,
+                                       ctx->device_loops ? ctx->aux : nullptr);
         if (k < 0) return -1;
         l += k;
     }
@@ -516,7 +518,8 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
         PicGeom Gm = ctx->pg;
         Gm.metal = ctx->d_pic_metal;
         const int k =
-            launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, kPcgIter, 1e-6, ctx->stream, ctx->aux);
+            launch_pic_solve_masked(Gm, ctx->d_picinst + n_plain, n_masked, kPcgIter, 1e-6, ctx->stream,
+                                    ctx->device_loops ? ctx->aux : nullptr);
         if (k < 0) return -1;
         launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
         l += k + 1;
@@ -660,20 +663,28 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
             if (!ctx->graph || key != ctx->graph_key) {
                 drop_graph(ctx);
                 cudaGraph_t g = nullptr;
-                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                 int64_t l = 0;
-                const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked) : 0;
-                l += lp;
-                l += step_launch(ctx, grp, tiles, chunk);
-                launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
-                l += 1;
-                const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-                if (ce == cudaSuccess && lp < 0) {
-                    cudaGraphDestroy(g);
+                // with device-controlled solve loops first; if they cannot be
+                // built, once more with the fixed pass sequences
+                for (int attempt = 0;; ++attempt) {
+                    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                    const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked) : 0;
+                    l = lp + step_launch(ctx, grp, tiles, chunk);
+                    launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
+                    l += 1;
+                    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+                    if (lp >= 0) {
+                        if (ce != cudaSuccess)
+                            return fail(ctx, MUCITE_E_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+                        break;
+                    }
+                    if (ce == cudaSuccess) cudaGraphDestroy(g);
+                    g = nullptr;
                     cudaGetLastError();
-                    return fail(ctx, MUCITE_E_CUDA, "graph capture of the solve loop failed");
+                    if (attempt > 0 || !ctx->device_loops)
+                        return fail(ctx, MUCITE_E_CUDA, "graph capture of the solve loop failed");
+                    ctx->device_loops = false;
                 }
-                if (ce != cudaSuccess) return fail(ctx, MUCITE_E_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
                 const cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
                 cudaGraphDestroy(g);
                 if (ie != cudaSuccess) {

@@ -260,75 +260,115 @@ __global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double
     else I.red[3] += 1.0;
 }
 
-// Tiled FP32 contraction C(m, n) = alpha * sum_k A(m, k) B(k, n) with strided
-// operands. A CTA computes a 64 x 64 output tile, 4 x 4 outputs per thread,
-// over 32-deep k slices double-buffered in shared memory: while a slice is
-// multiplied, the next one is already on its way from L2 into registers.
-// Small problems split the k range over the CTAs of a thread-block cluster
-// (`splits` CTAs along x, cluster rank = split): each CTA leaves its partial
-// tile in its shared memory and, after a cluster barrier, CTA r adds the
-// partials of its share of the rows through distributed shared memory in
-// rank order. Every output's sum has a fixed order, so results are
-// deterministic.
-template <bool A_M_CONTIG, bool B_N_CONTIG>
-__global__ void __launch_bounds__(256, 2) dst_gemm_kernel(DstGemm g, const PicInst *insts, int splits)
+// DST-I contractions of the fast solve with the sine matrix's symmetry:
+// with S[j][k] = sin(pi (j+1)(k+1) / (M+1)) (0-based), row M-1-j equals row j
+// in the even columns k = 2c and its negative in the odd ones k = 2c+1
+// (S[M-1-j][k] = (-1)^k S[j][k]), and S is symmetric. So each transform is
+// two contractions over H = ceil(M/2) terms instead of one over M, half the
+// arithmetic:
+//   forward (kInv = false), hat[i][k] = alpha sum_j r[j][i] S[j][k]:
+//     hat[i][2c]   = alpha sum_{j<H} (r[j][i] + r[M-1-j][i]) S[j][2c]
+//     hat[i][2c+1] = alpha sum_{j<H} (r[j][i] - r[M-1-j][i]) S[j][2c+1]
+//   inverse (kInv = true), d[j][i] = sum_k S[j][k] hat[i][k], for j < H:
+//     O = sum_{c<H} S[2c][j] hat[i][2c], E = sum_{c<H} S[2c+1][j] hat[i][2c+1],
+//     d[j][i] = O + E, d[M-1-j][i] = O - E,
+// where for odd M the middle row j = H-1 pairs with itself (r enters once;
+// S[H-1][2c+1] = 0). A CTA computes a 64 x 64 tile of both sums, 4 x 4
+// outputs of each per thread, over 16-deep k slices double-buffered in
+// shared memory. Small problems split the k range over the CTAs of a
+// thread-block cluster (`splits` CTAs along x, cluster rank = split): each
+// CTA leaves its partial tiles in its shared memory and, after a cluster
+// barrier, CTA r adds the partials of its share of the rows through
+// distributed shared memory in rank order. Every output's sum has a fixed
+// order, so results are deterministic.
+template <bool kInv>
+__global__ void __launch_bounds__(256, 2) dst_sym_kernel(PicGeom G, const PicInst *insts, int splits, float alpha)
 {
-    constexpr int KS = 32, BM = 64, BN = 64, PAD = 4;
-    constexpr int LA = BM * KS / 256, LB = KS * BN / 256;
+    constexpr int KS = 16, BM = 64, BN = 64, PAD = 4;
+    constexpr int L = BM * KS / 256; // elements of each operand tile loaded per thread per slice (BM == BN)
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return; // uniform over a cluster: its CTAs share blockIdx.z
-    const float *A = g.a_is_S ? g.S : (g.a_sel == 0 ? I.r32 : I.hat);
-    const float *B = g.b_is_S ? g.S : (g.b_sel == 0 ? I.r32 : I.hat);
-    float *C = g.c_sel == 1 ? I.hat : I.d32;
-    __shared__ __align__(16) float smem[2 * KS * (BM + PAD) + 2 * KS * (BN + PAD)];
-    float(*As)[KS][BM + PAD] = reinterpret_cast<float(*)[KS][BM + PAD]>(smem);
-    float(*Bs)[KS][BN + PAD] = reinterpret_cast<float(*)[KS][BN + PAD]>(smem + 2 * KS * (BM + PAD));
+    const int M = G.M, Nu = G.Nu, H = (M + 1) / 2;
+    const float *S = G.S;
+    const float *R = kInv ? I.hat : I.r32;
+    // operand tiles [buffer][set][k][m or n]; set 0: the even-column sum, 1: the odd-column sum
+    __shared__ __align__(16) float smem[2 * 2 * KS * (BM + PAD) * 2];
+    float(*As)[2][KS][BM + PAD] = reinterpret_cast<float(*)[2][KS][BM + PAD]>(smem);
+    float(*Bs)[2][KS][BN + PAD] = reinterpret_cast<float(*)[2][KS][BN + PAD]>(smem + 2 * 2 * KS * (BM + PAD));
     const int tid = threadIdx.x;
     const int split = (int)(blockIdx.x % (unsigned)splits);
     const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x / (unsigned)splits) * BN;
+    const int Mo = kInv ? H : Nu, No = kInv ? Nu : H;
     const int tx = tid & 15, ty = tid >> 4;
-    const int nsl = (g.K + KS - 1) / KS, per = (nsl + splits - 1) / splits;
-    const int kb = split * per * KS, ke = min(g.K, (split + 1) * per * KS);
-    float ra[LA], rb[LB];
+    const int nsl = (H + KS - 1) / KS, per = (nsl + splits - 1) / splits;
+    const int kb = split * per * KS, ke = min(H, (split + 1) * per * KS);
+    float a0[L], a1[L], b0[L], b1[L];
     auto load = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < LA; ++r) {
-            const int e = tid + 256 * r;
-            int mm, kk;
-            if (A_M_CONTIG) { mm = e & (BM - 1); kk = e / BM; }
-            else { kk = e % KS; mm = e / KS; }
+        for (int q = 0; q < L; ++q) {
+            const int e = tid + 256 * q;
+            const int mm = e & (BM - 1), kk = e / BM; // A: consecutive threads along m
             const int gm = m0 + mm, gk = k0 + kk;
-            ra[r] = (gm < g.Mo && gk < ke) ? A[(size_t)gm * g.a_sm + (size_t)gk * g.a_sk] : 0.0f;
+            float x0 = 0.0f, x1 = 0.0f;
+            if (gm < Mo && gk < ke) {
+                if (kInv) {
+                    // A(j, c) = S[2c][j], S[2c+1][j]
+                    x0 = S[(size_t)(2 * gk) * M + gm];
+                    x1 = 2 * gk + 1 < M ? S[(size_t)(2 * gk + 1) * M + gm] : 0.0f;
+                } else {
+                    // A(i, j) = r[j][i] +- r[M-1-j][i]
+                    const float u = R[(size_t)gk * Nu + gm];
+                    const int jm = M - 1 - gk;
+                    const float v = jm != gk ? R[(size_t)jm * Nu + gm] : 0.0f;
+                    x0 = u + v;
+                    x1 = u - v;
+                }
+            }
+            a0[q] = x0;
+            a1[q] = x1;
         }
 #pragma unroll
-        for (int r = 0; r < LB; ++r) {
-            const int e = tid + 256 * r;
+        for (int q = 0; q < L; ++q) {
+            const int e = tid + 256 * q;
             int nn, kk;
-            if (B_N_CONTIG) { nn = e & (BN - 1); kk = e / BN; }
-            else { kk = e % KS; nn = e / KS; }
+            if (kInv) { kk = e % KS; nn = e / KS; } // B = hat: consecutive threads along k
+            else { nn = e & (BN - 1); kk = e / BN; } // B = S rows: along n
             const int gn = n0 + nn, gk = k0 + kk;
-            rb[r] = (gn < g.No && gk < ke) ? B[(size_t)gk * g.b_sk + (size_t)gn * g.b_sn] : 0.0f;
+            float y0 = 0.0f, y1 = 0.0f;
+            if (gn < No && gk < ke) {
+                if (kInv) {
+                    // B(c, i) = hat[i][2c], hat[i][2c+1]
+                    y0 = R[(size_t)gn * M + 2 * gk];
+                    y1 = 2 * gk + 1 < M ? R[(size_t)gn * M + 2 * gk + 1] : 0.0f;
+                } else {
+                    // B(j, c) = S[j][2c], S[j][2c+1]
+                    y0 = S[(size_t)gk * M + 2 * gn];
+                    y1 = 2 * gn + 1 < M ? S[(size_t)gk * M + 2 * gn + 1] : 0.0f;
+                }
+            }
+            b0[q] = y0;
+            b1[q] = y1;
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < LA; ++r) {
-            const int e = tid + 256 * r;
-            int mm, kk;
-            if (A_M_CONTIG) { mm = e & (BM - 1); kk = e / BM; }
-            else { kk = e % KS; mm = e / KS; }
-            As[buf][kk][mm] = ra[r];
+        for (int q = 0; q < L; ++q) {
+            const int e = tid + 256 * q;
+            const int mm = e & (BM - 1), kk = e / BM;
+            As[buf][0][kk][mm] = a0[q];
+            As[buf][1][kk][mm] = a1[q];
         }
 #pragma unroll
-        for (int r = 0; r < LB; ++r) {
-            const int e = tid + 256 * r;
+        for (int q = 0; q < L; ++q) {
+            const int e = tid + 256 * q;
             int nn, kk;
-            if (B_N_CONTIG) { nn = e & (BN - 1); kk = e / BN; }
-            else { kk = e % KS; nn = e / KS; }
-            Bs[buf][kk][nn] = rb[r];
+            if (kInv) { kk = e % KS; nn = e / KS; }
+            else { nn = e & (BN - 1); kk = e / BN; }
+            Bs[buf][0][kk][nn] = b0[q];
+            Bs[buf][1][kk][nn] = b1[q];
         }
     };
-    float acc[4][4] = {};
+    float acc0[4][4] = {}, acc1[4][4] = {};
     if (kb < ke) {
         load(kb);
         store(0);
@@ -339,52 +379,83 @@ __global__ void __launch_bounds__(256, 2) dst_gemm_kernel(DstGemm g, const PicIn
             if (more) load(k0 + KS);
 #pragma unroll
             for (int kk = 0; kk < KS; ++kk) {
-                const float4 a = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-                const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                const float4 p0 = *reinterpret_cast<const float4 *>(&As[buf][0][kk][ty * 4]);
+                const float4 p1 = *reinterpret_cast<const float4 *>(&As[buf][1][kk][ty * 4]);
+                const float4 q0 = *reinterpret_cast<const float4 *>(&Bs[buf][0][kk][tx * 4]);
+                const float4 q1 = *reinterpret_cast<const float4 *>(&Bs[buf][1][kk][tx * 4]);
+                const float ua[4] = {p0.x, p0.y, p0.z, p0.w}, ub[4] = {p1.x, p1.y, p1.z, p1.w};
+                const float va[4] = {q0.x, q0.y, q0.z, q0.w}, vb[4] = {q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                    for (int v = 0; v < 4; ++v) {
+                        acc0[u][v] = fmaf(ua[u], va[v], acc0[u][v]);
+                        acc1[u][v] = fmaf(ub[u], vb[v], acc1[u][v]);
+                    }
             }
             if (more) store(buf ^ 1);
             __syncthreads();
             buf ^= 1;
         }
     }
+    // epilogue for output (row m, column n) of the tile with sums x0 (even
+    // columns / O) and x1 (odd columns / E)
+    auto put = [&](int mm, int nn, float x0, float x1) {
+        const int gm = m0 + mm, gn = n0 + nn;
+        if (gm >= Mo || gn >= No) return;
+        if (kInv) {
+            float *D = I.d32;
+            D[(size_t)gm * Nu + gn] = x0 + x1;
+            const int jm = M - 1 - gm;
+            if (jm != gm) D[(size_t)jm * Nu + gn] = x0 - x1;
+        } else {
+            float *D = I.hat + (size_t)gm * M;
+            D[2 * gn] = alpha * x0;
+            if (2 * gn + 1 < M) D[2 * gn + 1] = alpha * x1;
+        }
+    };
     if (splits == 1) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int gm = m0 + ty * 4 + u;
-            if (gm >= g.Mo) continue;
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int gn = n0 + tx * 4 + v;
-                if (gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * acc[u][v];
-            }
-        }
+            for (int v = 0; v < 4; ++v) put(ty * 4 + u, tx * 4 + v, acc0[u][v], acc1[u][v]);
         return;
     }
-    // split-K: partial tile to shared memory (the slice buffers are free after
-    // the loop's last barrier), rank-ordered sum over the cluster
+    // split-K: partial tiles to shared memory (the slice buffers are free
+    // after the loop's last barrier), rank-ordered sums over the cluster
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    float(*Ps)[BN + PAD] = reinterpret_cast<float(*)[BN + PAD]>(smem);
+    float(*Ps)[BM][BN + PAD] = reinterpret_cast<float(*)[BM][BN + PAD]>(smem);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Ps[ty * 4 + u][tx * 4 + v] = acc[u][v];
+        for (int v = 0; v < 4; ++v) {
+            Ps[0][ty * 4 + u][tx * 4 + v] = acc0[u][v];
+            Ps[1][ty * 4 + u][tx * 4 + v] = acc1[u][v];
+        }
     cluster.sync();
     const int rows = BM / splits, r0 = split * rows;
     for (int e = tid; e < rows * BN; e += 256) {
         const int rr = r0 + e / BN, cc = e % BN;
-        float sum = 0.0f;
-        for (int q = 0; q < splits; ++q) {
-            const float *rp = cluster.map_shared_rank(&Ps[0][0], (unsigned)q);
-            sum += rp[rr * (BN + PAD) + cc];
+        // all remote reads in flight together, then added in rank order
+        float y0[8], y1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < splits) {
+                const float *rp = cluster.map_shared_rank(&Ps[0][0][0], (unsigned)q);
+                y0[q] = rp[rr * (BN + PAD) + cc];
+                y1[q] = rp[BM * (BN + PAD) + rr * (BN + PAD) + cc];
+            }
         }
-        const int gm = m0 + rr, gn = n0 + cc;
-        if (gm < g.Mo && gn < g.No) C[(size_t)gm * g.c_sm + (size_t)gn * g.c_sn] = g.alpha * sum;
+        float x0 = 0.0f, x1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < splits) {
+                x0 += y0[q];
+                x1 += y1[q];
+            }
+        }
+        put(rr, cc, x0, x1);
     }
     cluster.sync(); // partials stay readable until every CTA of the cluster is done
 }
@@ -579,8 +650,8 @@ void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int 
 }
 
 // Launch of a contraction with `splits` CTAs per cluster along x.
-void launch_gemm(void (*kern)(DstGemm, const PicInst *, int), dim3 grid, int splits, const DstGemm &g,
-                 const PicInst *d_insts, cudaStream_t s)
+void launch_sym(void (*kern)(PicGeom, const PicInst *, int, float), dim3 grid, int splits, const PicGeom &G,
+                const PicInst *d_insts, float alpha, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
@@ -594,36 +665,28 @@ void launch_gemm(void (*kern)(DstGemm, const PicInst *, int), dim3 grid, int spl
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, g, d_insts, splits);
+    cudaLaunchKernelEx(&cfg, kern, G, d_insts, splits, alpha);
 }
 
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
-    DstGemm fwd{}, inv{};
-    // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
-    fwd.S = G.S; fwd.a_is_S = 0; fwd.a_sel = 0; fwd.b_is_S = 1; fwd.c_sel = 1;
-    fwd.Mo = G.Nu; fwd.No = G.M; fwd.K = G.M;
-    fwd.a_sm = 1; fwd.a_sk = G.Nu; fwd.b_sk = G.M; fwd.b_sn = 1; fwd.c_sm = G.M; fwd.c_sn = 1;
-    fwd.alpha = (float)(2.0 / (G.M + 1));
-    // d32[j][i] = sum_k S[j][k] hat[i][k]
-    inv.S = G.S; inv.a_is_S = 1; inv.b_is_S = 0; inv.b_sel = 1; inv.c_sel = 2;
-    inv.Mo = G.M; inv.No = G.Nu; inv.K = G.M;
-    inv.a_sm = G.M; inv.a_sk = 1; inv.b_sk = 1; inv.b_sn = G.M; inv.c_sm = G.Nu; inv.c_sn = 1;
-    inv.alpha = 1.0f;
-    // split the k range over a cluster of 2 or 4 CTAs while the 64 x 64
+    // split the k range over a cluster of 2 to 8 CTAs while the 64 x 64
     // tiles would leave the SMs without a second resident CTA
     const int sms = G.n_sm > 0 ? G.n_sm : 148;
-    const int64_t tiles = (int64_t)((G.M + 63) / 64) * ((G.Nu + 63) / 64) * n_inst;
+    const int H = (G.M + 1) / 2;
+    const int64_t tiles = (int64_t)((H + 63) / 64) * ((G.Nu + 63) / 64) * n_inst;
     int splits = 1;
-    while (splits < 4 && tiles * splits < 2 * sms && (G.M + 31) / 32 >= 4 * splits) splits *= 2;
-    const dim3 gf((unsigned)(((G.M + 63) / 64) * splits), (G.Nu + 63) / 64, n_inst);
-    const dim3 gi((unsigned)(((G.Nu + 63) / 64) * splits), (G.M + 63) / 64, n_inst);
-    launch_gemm(dst_gemm_kernel<true, true>, gf, splits, fwd, d_insts, s);
+    while (splits < 8 && tiles * splits < 2 * sms && (H + 15) / 16 >= 4 * splits) splits *= 2;
+    const dim3 gf((unsigned)(((H + 63) / 64) * splits), (G.Nu + 63) / 64, n_inst);
+    const dim3 gi((unsigned)(((G.Nu + 63) / 64) * splits), (H + 63) / 64, n_inst);
+    // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
+    launch_sym(dst_sym_kernel<false>, gf, splits, G, d_insts, (float)(2.0 / (G.M + 1)), s);
     if (G.Nu <= kThRows)
         thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
     else
         thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    launch_gemm(dst_gemm_kernel<false, false>, gi, splits, inv, d_insts, s);
+    // d32[j][i] = sum_k S[j][k] hat[i][k]
+    launch_sym(dst_sym_kernel<true>, gi, splits, G, d_insts, 1.0f, s);
     return 3;
 }
 

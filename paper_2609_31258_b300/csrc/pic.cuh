@@ -53,14 +53,6 @@ struct DepositArgs {
     unsigned long long *Q;
 };
 
-struct DstGemm {
-    const float *S;
-    int a_is_S, a_sel, b_is_S, b_sel, c_sel; // sel: 0 = r32, 1 = hat, 2 = d32
-    int Mo, No, K;
-    int64_t a_sm, a_sk, b_sk, b_sn, c_sm, c_sn;
-    float alpha;
-};
-
 // Batched over instances: tile t of 256 packs belongs to the instance i with
 // tile_start[i] <= t < tile_start[i + 1].
 void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,
