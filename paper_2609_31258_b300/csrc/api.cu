@@ -208,6 +208,7 @@ void free_instance(Instance &I)
     dfree(I.pic.p64);
     dfree(I.pic.part);
     dfree(I.pic.ticket);
+    dfree(I.pic.Qn);
     I = Instance();
 }
 
@@ -467,7 +468,7 @@ DepositArgs deposit_args(const mucite_ctx *ctx, const Instance &I)
 
 // Upload the descriptors of a space-charge group (outside any capture).
 mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in, int &total_tiles,
-                         int &n_masked)
+                         int &n_masked, bool into_next = false)
 {
     // maskless instances first, mask-aware ones after: two batched solves
     std::vector<Instance *> grp;
@@ -483,6 +484,7 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in,
     int64_t total = 0;
     for (size_t k = 0; k < n; ++k) {
         dep[k] = deposit_args(ctx, *grp[k]);
+        if (into_next) dep[k].Q = grp[k]->pic.Qn;
         pi[k] = grp[k]->pic;
         tiles[k] = (int32_t)total;
         total += (grp[k]->n_slots + 255) / 256;
@@ -500,13 +502,21 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in,
 // number of launches for any number of instances. Issued directly, passes
 // after convergence still launch (and return at once), so the caps are kept
 // near what the warm-started solves need; under graph capture the solve loops
-// become device-controlled while nodes that stop at convergence. Returns the
-// launches issued, or -1 when a captured loop could not be built.
-int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked)
+// become device-controlled while nodes that stop at convergence. With take,
+// the charge is not deposited here but taken over from Qn, where the previous
+// step launch deposited it. Returns the launches issued, or -1 when a
+// captured loop could not be built.
+int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked, bool take = false)
 {
-    launch_pic_prepare(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
-    launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
-    int64_t l = 2;
+    int64_t l = 1;
+    if (take) {
+        // the charge was deposited by the previous step launch (into Qn)
+        launch_pic_take(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
+    } else {
+        launch_pic_prepare(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
+        launch_deposit(ctx->d_dep, ctx->d_dep_tiles, n_inst, total_tiles, ctx->stream);
+        ++l;
+    }
     const int n_plain = n_inst - n_masked;
     if (n_plain > 0) {
         const int k = launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream,
@@ -568,7 +578,8 @@ mucite_status ensure_rf(mucite_ctx *ctx, size_t floats)
 }
 
 // Upload the step descriptors of a group (clocks, slot counts, tiles).
-mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, int chunk, int &total_tiles)
+mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, int chunk, int &total_tiles,
+                          bool deposit_next = false)
 {
     const size_t n = grp.size();
     std::vector<InstF32> host(n);
@@ -580,6 +591,8 @@ mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, i
         host[k].n_slots = I->n_slots;
         host[k].step0 = I->step;
         host[k].rf = ctx->d_rf + k * (size_t)(2 * chunk + 1);
+        host[k].dep_q = deposit_next ? I->pic.Qn : nullptr;
+        host[k].dep_qw = (int64_t)I->ion.charge * I->src.weight;
         tiles[k] = (int32_t)total;
         total += (I->n_slots + ctx->threads - 1) / ctx->threads;
     }
@@ -653,12 +666,24 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 key.push_back(I);
                 key.push_back((const void *)(intptr_t)I->n_slots);
             }
+            // each replay's step launch deposits the charge its successor's
+            // solve needs (into Qn) while the positions are in registers;
+            // the first replay takes the charge deposited here
+            bool fused = P0 > 0;
+            for (Instance *I : grp) fused = fused && I->pic.Qn != nullptr;
+            key.push_back((const void *)(intptr_t)fused);
             int tiles = 0, ptiles = 0, pmasked = 0;
-            st = step_upload(ctx, grp, chunk, tiles);
+            st = step_upload(ctx, grp, chunk, tiles, fused);
             if (st != MUCITE_OK) return st;
             if (P0 > 0) {
-                st = pic_upload(ctx, grp, ptiles, pmasked);
+                st = pic_upload(ctx, grp, ptiles, pmasked, fused);
                 if (st != MUCITE_OK) return st;
+            }
+            if (fused) {
+                launch_pic_clear_next(ctx->pg, ctx->d_picinst, (int)n, ctx->stream);
+                launch_deposit(ctx->d_dep, ctx->d_dep_tiles, (int)n, ptiles, ctx->stream);
+                ctx->launches += 2;
+                CKL();
             }
             if (!ctx->graph || key != ctx->graph_key) {
                 drop_graph(ctx);
@@ -668,7 +693,7 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 // built, once more with the fixed pass sequences
                 for (int attempt = 0;; ++attempt) {
                     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-                    const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked) : 0;
+                    const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked, fused) : 0;
                     l = lp + step_launch(ctx, grp, tiles, chunk);
                     launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
                     l += 1;
@@ -1043,6 +1068,7 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
             CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         }
         CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
+        if (run->precision == MUCITE_FP32) CK(cudaMalloc(&I.pic.Qn, nn * sizeof(unsigned long long)));
         if (run->precision == MUCITE_FP64) {
             CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));
             CK(cudaMalloc(&I.pic.ez64, nn * sizeof(double)));

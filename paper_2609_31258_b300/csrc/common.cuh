@@ -135,6 +135,8 @@ struct InstF32 {
     const float2 *esc;         // space-charge field (E_r, E_z) on the PIC grid or NULL
     int pnr, pnz;
     float psr;                 // (pnr - 1) * 2^-30
+    unsigned long long *dep_q; // charge grid the launch deposits its active packs into at the end, or NULL
+    int64_t dep_qw;            // charge number * weight of a pack (its CIC contributions: dep_qw w_r w_z)
     unsigned long long *counters; // [0] pack-steps, [1] collisions, [2] candidate-cap hits
 };
 

@@ -25,28 +25,12 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "deposit.cuh"
 #include "pic.cuh"
 
 namespace mucite {
 
 namespace {
-
-// floor(sqrt(v)) for v < 2^62, exact. An FP32 estimate (within ~2^-23
-// relative, i.e. below 2^8 for v < 2^62) refined by one Newton correction
-// from the exact integer residual v - r0^2 leaves r within 1 of the answer;
-// the integer tests settle it. FP32 keeps the deposit off the slow FP64 pipe.
-__device__ __forceinline__ uint64_t isqrt_floor(uint64_t v)
-{
-    if (v == 0) return 0;
-    const uint64_t r0 = (uint64_t)__fsqrt_rn((float)v);
-    const int64_t e = (int64_t)(v - r0 * r0); // |e| <= 2^9 r0 + 2^16, exact in 64 bits
-    int64_t r = (int64_t)r0 + (int64_t)__float2ll_rn((float)e / (2.0f * (float)r0));
-    if (r < 0) r = 0;
-    uint64_t u = (uint64_t)r;
-    while (u * u > v) --u;
-    while ((u + 1) * (u + 1) <= v) ++u;
-    return u;
-}
 
 __device__ __forceinline__ int32_t q32p(double v)
 {
@@ -89,23 +73,7 @@ __device__ __forceinline__ bool deposit_weights(const DepositArgs &A, int64_t p,
         yq = q32p(__dmul_rn(((const double *)A.y)[p], A.sx));
         zq = q32p(__dmul_rn(__dsub_rn(((const double *)A.z)[p], A.gz0), A.sz));
     }
-    const uint64_t r2 = (uint64_t)((int64_t)xq * xq) + (uint64_t)((int64_t)yq * yq);
-    const uint64_t r = isqrt_floor(r2);
-    if (r >= (1ULL << 30) || zq < 0 || zq > (1 << 30)) return false;
-    const uint64_t tr = r * (uint64_t)(A.pnr - 1);
-    const uint64_t tz = (uint64_t)zq * (uint64_t)(A.pnz - 1);
-    int64_t i = (int64_t)(tr >> 30), j = (int64_t)(tz >> 30);
-    int64_t fr = (int64_t)((tr & ((1ULL << 30) - 1)) >> 15);
-    int64_t fz = (int64_t)((tz & ((1ULL << 30) - 1)) >> 15);
-    if (i > A.pnr - 2) { i = A.pnr - 2; fr = 1 << 15; }
-    if (j > A.pnz - 2) { j = A.pnz - 2; fz = 1 << 15; }
-    const int64_t wr0 = (1 << 15) - fr, wr1 = fr, wz0 = (1 << 15) - fz, wz1 = fz;
-    cell = (uint32_t)(j * A.pnr + i);
-    w[0] = (unsigned long long)(A.qw * wr0 * wz0);
-    w[1] = (unsigned long long)(A.qw * wr1 * wz0);
-    w[2] = (unsigned long long)(A.qw * wr0 * wz1);
-    w[3] = (unsigned long long)(A.qw * wr1 * wz1);
-    return true;
+    return cic_lattice(xq, yq, zq, A.pnr, A.pnz, A.qw, cell, w);
 }
 
 // Charge deposit of one 256-pack tile. Packs of a beam crowd into few
@@ -178,6 +146,28 @@ __global__ void __launch_bounds__(256) pic_prepare_kernel(PicGeom G, const PicIn
         I.Q[e] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x < 8) I.red[threadIdx.x] = 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
+}
+
+__global__ void __launch_bounds__(256) pic_take_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.y];
+    const int64_t n = (int64_t)G.pnr * G.pnz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        I.Q[e] = I.Qn[e];
+        I.Qn[e] = 0ull;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 8) I.red[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
+}
+
+__global__ void __launch_bounds__(256) pic_clear_next_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.y];
+    const int64_t n = (int64_t)G.pnr * G.pnz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        I.Qn[e] = 0ull;
 }
 
 // ||b||^2 over the unknowns; also clears the convergence flag and counters.
@@ -640,6 +630,20 @@ void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cu
     const int64_t nn = (int64_t)G.pnr * G.pnz;
     const unsigned bx = (unsigned)std::min<int64_t>((nn + 255) / 256, 512);
     pic_prepare_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(G, d_insts);
+}
+
+void launch_pic_take(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+{
+    const int64_t nn = (int64_t)G.pnr * G.pnz;
+    const unsigned bx = (unsigned)std::min<int64_t>((nn + 255) / 256, 512);
+    pic_take_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(G, d_insts);
+}
+
+void launch_pic_clear_next(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+{
+    const int64_t nn = (int64_t)G.pnr * G.pnz;
+    const unsigned bx = (unsigned)std::min<int64_t>((nn + 255) / 256, 512);
+    pic_clear_next_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(G, d_insts);
 }
 
 void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,

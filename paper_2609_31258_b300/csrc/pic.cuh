@@ -24,6 +24,8 @@ struct PicGeom {
 // Per-instance buffers of the space-charge solve.
 struct PicInst {
     unsigned long long *Q;   // [pnz][pnr] node charge, units e * 2^-30
+    unsigned long long *Qn;  // [pnz][pnr] charge deposited by the step kernels at the end of a macro
+                             // step's launch, taken over by the next solve (FP32 graph replays) or NULL
     double *phi;             // [pnz][pnr] potential (zero on the Dirichlet boundary)
     float *r32;              // [M][Nu] residual in FP32
     float *hat;              // [Nu][M] transformed residual / correction
@@ -58,6 +60,11 @@ struct DepositArgs {
 void launch_deposit(const DepositArgs *d_args, const int32_t *d_tile_start, int n_inst, int total_tiles,
                     cudaStream_t s);
 void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
+// As launch_pic_prepare, but the charge of the solve is taken from Qn
+// (Q <- Qn, Qn <- 0) instead of being cleared for a deposit.
+void launch_pic_take(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
+// Clears Qn (before a standalone deposit into it).
+void launch_pic_clear_next(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 // Returns the number of kernel launches issued. When `s` is being captured
 // into a CUDA graph and `aux` is a stream of this device, the correction
 // passes become the body of a device-controlled while loop (a conditional

@@ -23,6 +23,7 @@
 // Positions, the mask lookup and the classification are integer or IEEE
 // round-to-nearest FP32 operations without contraction, so they decide the
 // same classes as any other implementation of the same lattice rules.
+#include "deposit.cuh"
 #include "kernels.cuh"
 
 namespace mucite {
@@ -394,6 +395,21 @@ __device__ __forceinline__ void add_counters(const InstF32 &P, unsigned n_steps_
     }
 }
 
+// End-of-launch charge deposit of a pack that is still active (the charge
+// the next space-charge solve needs, deposited while the positions are in
+// registers): the same integer CIC contributions as the standalone deposit.
+__device__ __forceinline__ void deposit_at_end(const InstF32 &P, int32_t xq, int32_t yq, int32_t zq)
+{
+    uint32_t cell;
+    unsigned long long w[4];
+    if (!cic_lattice(xq, yq, zq, P.pnr, P.pnz, P.dep_qw, cell, w)) return;
+    unsigned long long *Q = P.dep_q + cell;
+    if (w[0]) atomicAdd(Q, w[0]);
+    if (w[1]) atomicAdd(Q + 1, w[1]);
+    if (w[2]) atomicAdd(Q + P.pnr, w[2]);
+    if (w[3]) atomicAdd(Q + P.pnr + 1, w[3]);
+}
+
 // Kick and drift of step n with kick (kx, ky, kz) evaluated at x_n (RK4:
 // the first stage), then the lattice radius and class at x_{n+1}.
 template <bool kExtras>
@@ -521,6 +537,8 @@ __device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P
         if (st[u] != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st[u];
             P.t_term[p] = (int32_t)(P.step0 + kd[u]);
+        } else if (P.dep_q != nullptr) {
+            deposit_at_end(P, xq[u], yq[u], zq[u]);
         }
     }
     add_counters(P, n_steps_done, 0u, 0u);
@@ -630,6 +648,8 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         if (st != MUCITE_ACTIVE) {
             P.status[p] = (uint8_t)st;
             P.t_term[p] = (int32_t)(P.step0 + k);
+        } else if (P.dep_q != nullptr) {
+            deposit_at_end(P, xq, yq, zq);
         }
     }
     add_counters(P, owned ? (unsigned)k : 0u, n_coll, n_ovf);
