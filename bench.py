@@ -598,6 +598,8 @@ def _space_charge(args, local, stream, dev):
             ctx.set_launch_mode(0, False)
         ctx.load_fields(w.fields)
         ctx.inject(0, w.ion, w.source, run, capacity=args.pic_packs + 100_000)
+        # the library's autotuner picks the launch shape (state restored after)
+        tuning = None if args.no_autotune else ctx.autotune([0], 200)
         ctx.step(0, K)  # warm-up of the timed call's shape (graph capture)
         torch.cuda.synchronize(dev)
         T0 = ctx.tally(0)
@@ -610,15 +612,16 @@ def _space_charge(args, local, stream, dev):
         pr = ctx.pic_read(0) if run.pic_interval else {}
         rel = (pr.get("rel_residual"), pr.get("iterations"))
         ctx.close()
-        return a.elapsed_time(b), T1["pack_steps"] - T0["pack_steps"], rel
+        return a.elapsed_time(b), T1["pack_steps"] - T0["pack_steps"], rel, tuning
 
-    ms, ps, rel = timed(w.run)
-    ms0, _, _ = timed(dataclasses.replace(w.run, pic_interval=0))
+    ms, ps, rel, tuning = timed(w.run)
+    ms0, _, _, _ = timed(dataclasses.replace(w.run, pic_interval=0))
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "packs": args.pic_packs, "micro_steps": K, "ms": ms,
             "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
             "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
             "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024",
-            "launch": "direct (fixed solve passes)" if args.pic_direct else "graph-replayed macro steps"}
+            "launch": "direct (fixed solve passes)" if args.pic_direct else "graph-replayed macro steps",
+            "tuning": tuning}
 
 
 def _paper_grid(args, local, stream, dev):
