@@ -130,6 +130,7 @@ template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const
     return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
            cudaSuccess;
 }
+
 // E_SCE by central differences of Phi.
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 
