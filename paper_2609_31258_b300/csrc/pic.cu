@@ -557,6 +557,54 @@ __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicIn
     }
 }
 
+// Tridiagonal solve of one axial mode k per block by parallel cyclic
+// reduction: row i of mode k reads a_i x_{i-1} + d_ik x_i + c_i x_{i+1} = h_i
+// with d_ik = -(a_i + c_i + A_i lambda_k), lambda_k = 4 sin^2(pi k / (2 (M+1)))
+// (the z eigenvalue of mode k; x_Nu = 0 at the outer radius). Every round
+// eliminates the couplings to the rows at distance s (s = 1, 2, 4, ...) from
+// each row with the rows at distance s, so after ceil(log2 Nu) rounds each
+// row stands alone: x_i = d_i / b_i. One thread per row (Nu <= 256), rows
+// past Nu are identity rows; the rounds run on shared memory, so the solve
+// costs 8 short rounds instead of a dependent chain of 2 Nu steps. The
+// systems are diagonally dominant, where cyclic reduction is stable.
+__global__ void __launch_bounds__(256) pcr_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ float sa[2][256], sb[2][256], sc[2][256], sd[2][256];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int k = blockIdx.x, i = threadIdx.x, n = G.Nu;
+    const float sn = sinpif((float)(k + 1) / (2.0f * (float)(G.M + 1)));
+    const float lam = 4.0f * sn * sn;
+    float a = 0.0f, b = 1.0f, c = 0.0f, d = 0.0f;
+    if (i < n) {
+        const float ai = (float)G.a[i], ci = (float)G.c[i];
+        a = ai; // a_0 = 0: no flux through the axis
+        c = i + 1 < n ? ci : 0.0f;
+        b = -(ai + ci + (float)G.A[i] * lam);
+        d = I.hat[(size_t)i * G.M + k];
+    }
+    int cur = 0;
+    sa[0][i] = a; sb[0][i] = b; sc[0][i] = c; sd[0][i] = d;
+    __syncthreads();
+    for (int st = 1; st < n; st <<= 1) {
+        const int lo = i - st, hi = i + st;
+        const bool hl = lo >= 0, hh = hi < 256;
+        const float am = hl ? sa[cur][lo] : 0.0f, bm = hl ? sb[cur][lo] : 1.0f;
+        const float cm = hl ? sc[cur][lo] : 0.0f, dm = hl ? sd[cur][lo] : 0.0f;
+        const float ap = hh ? sa[cur][hi] : 0.0f, bp = hh ? sb[cur][hi] : 1.0f;
+        const float cp = hh ? sc[cur][hi] : 0.0f, dp = hh ? sd[cur][hi] : 0.0f;
+        const float al = -__fdividef(a, bm), ga = -__fdividef(c, bp);
+        b = b + al * cm + ga * ap;
+        d = d + al * dm + ga * dp;
+        a = al * am;
+        c = ga * cp;
+        cur ^= 1;
+        sa[cur][i] = a; sb[cur][i] = b; sc[cur][i] = c; sd[cur][i] = d;
+        __syncthreads();
+    }
+    if (i < n) I.hat[(size_t)i * G.M + k] = __fdividef(d, b);
+}
+
 // Tridiagonal solve per axial mode k, in place on hat[i][k] (i = 0..Nu-1),
 // with the elimination factors of the fixed operator precomputed.
 __global__ void __launch_bounds__(256) thomas_kernel(PicGeom G, const PicInst *insts)
@@ -685,7 +733,13 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
     const dim3 gi((unsigned)(((G.Nu + 63) / 64) * splits), (H + 63) / 64, n_inst);
     // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
     launch_sym(dst_sym_kernel<false>, gf, splits, G, d_insts, (float)(2.0 / (G.M + 1)), s);
-    if (G.Nu <= kThRows)
+    // radial systems of 129..256 unknowns: cyclic reduction (a long Thomas
+    // chain); up to 128 the 8-mode Thomas blocks are as fast and more
+    // accurate in FP32. The choice depends on the grid only, so batched and
+    // single-instance solves of the same grid take the same arithmetic.
+    if (G.Nu > 128 && G.Nu <= 256)
+        pcr_kernel<<<dim3(G.M, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    else if (G.Nu <= kThRows)
         thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
     else
         thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);

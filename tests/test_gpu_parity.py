@@ -283,12 +283,14 @@ def test_tally_bit_exact(mc, orc):
 # ---------------------------------------------------------------------------
 # Poisson solve
 # ---------------------------------------------------------------------------
-# (300, 129): more than 256 radial unknowns, the tridiagonal sweeps on global
-# memory; the others use the shared-memory staged sweeps. (3, 5) and (7, 4):
-# fewer unknowns than one tile or one batch of the sweeps' row prefetch;
-# (33, 65): one ragged tile, k range not split; (65, 257) and (300, 129): k
-# range split over clusters of 2 CTAs; (256, 1024): over clusters of 4.
-@pytest.mark.parametrize("shape", [(65, 257), (256, 1024), (300, 129), (3, 5), (7, 4), (33, 65)])
+# Radial systems: (300, 129) has more than 256 radial unknowns (tridiagonal
+# sweeps on global memory); (256, 1024) and (150, 257) have 129..256 (cyclic
+# reduction, 150 not a power of two); the others up to 128 (shared-memory
+# staged sweeps). (3, 5) and (7, 4): fewer unknowns than one tile or one batch
+# of the sweeps' row prefetch; (33, 65): one ragged tile, k range not split;
+# (300, 129): k range split over clusters of 2 CTAs, (65, 257) of 4,
+# (256, 1024) of 8.
+@pytest.mark.parametrize("shape", [(65, 257), (256, 1024), (300, 129), (3, 5), (7, 4), (33, 65), (150, 257)])
 def test_poisson_matches_direct_solve(mc, orc, shape):
     from oracle import poisson
     pnr, pnz = shape
