@@ -209,6 +209,7 @@ void free_instance(Instance &I)
     dfree(I.pic.part);
     dfree(I.pic.ticket);
     dfree(I.pic.Qn);
+    dfree(I.pic.esc4);
     I = Instance();
 }
 
@@ -296,7 +297,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.rdet2 = (uint64_t)(rdet_q * rdet_q);
         P.hit = (float)r.hit_dist;
         if (I.has_pic) {
-            P.esc = I.pic.esc;
+            P.esc4 = I.pic.esc4;
             P.pnr = ctx->pg.pnr;
             P.pnz = ctx->pg.pnz;
             P.psr = (float)(ctx->pg.pnr - 1) * (1.0f / 1073741824.0f);
@@ -534,7 +535,8 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked, b
         launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
         l += k + 1;
     }
-    return l;
+    launch_esc_cells(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
+    return l + 1;
 }
 
 mucite_status pic_update_group(mucite_ctx *ctx, const std::vector<Instance *> &grp)
@@ -1068,7 +1070,12 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
             CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         }
         CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
-        if (run->precision == MUCITE_FP32) CK(cudaMalloc(&I.pic.Qn, nn * sizeof(unsigned long long)));
+        if (run->precision == MUCITE_FP32) {
+            const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
+            CK(cudaMalloc(&I.pic.Qn, nn * sizeof(unsigned long long)));
+            CK(cudaMalloc(&I.pic.esc4, nc * 2 * sizeof(float4)));
+            CK(cudaMemsetAsync(I.pic.esc4, 0, nc * 2 * sizeof(float4), ctx->stream));
+        }
         if (run->precision == MUCITE_FP64) {
             CK(cudaMalloc(&I.pic.er64, nn * sizeof(double)));
             CK(cudaMalloc(&I.pic.ez64, nn * sizeof(double)));
@@ -1208,7 +1215,8 @@ struct Snapshot {
 size_t pic_state_bytes(const mucite_ctx *ctx)
 {
     const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
-    return nn * (sizeof(unsigned long long) + sizeof(double) + sizeof(float2));
+    const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
+    return nn * (sizeof(unsigned long long) + sizeof(double) + sizeof(float2)) + nc * 2 * sizeof(float4);
 }
 
 mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
@@ -1229,6 +1237,7 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
     }
     S.counters.resize(3 * S.sel.size());
     const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
+    const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
     for (size_t k = 0; k < S.sel.size(); ++k) {
         Instance *I = S.sel[k];
         char *dst = S.d + S.off[k];
@@ -1238,6 +1247,8 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
             CK(cudaMemcpyAsync(q, I->pic.Q, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(q + nn * 8, I->pic.phi, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(q + nn * 16, I->pic.esc, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            if (I->pic.esc4)
+                CK(cudaMemcpyAsync(q + nn * 24, I->pic.esc4, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
         }
         CK(cudaMemcpyAsync(&S.counters[3 * k], I->d_counters, 3 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, ctx->stream));
@@ -1249,6 +1260,7 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
 mucite_status snapshot_restore(mucite_ctx *ctx, const Snapshot &S)
 {
     const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
+    const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
     for (size_t k = 0; k < S.sel.size(); ++k) {
         Instance *I = S.sel[k];
         const char *src = S.d + S.off[k];
@@ -1258,6 +1270,8 @@ mucite_status snapshot_restore(mucite_ctx *ctx, const Snapshot &S)
             CK(cudaMemcpyAsync(I->pic.Q, q, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(I->pic.phi, q + nn * 8, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(I->pic.esc, q + nn * 16, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            if (I->pic.esc4)
+                CK(cudaMemcpyAsync(I->pic.esc4, q + nn * 24, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
         }
         CK(cudaMemcpyAsync(I->d_counters, &S.counters[3 * k], 3 * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, ctx->stream));

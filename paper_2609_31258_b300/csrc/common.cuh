@@ -132,7 +132,8 @@ struct InstF32 {
     int64_t zexit_q;           // first lattice z counted as crossed
     uint64_t rdet2;            // (floor(r_det / R * 2^30))^2
     float hit;                 // electrode-hit distance [m]
-    const float2 *esc;         // space-charge field (E_r, E_z) on the PIC grid or NULL
+    const float4 *esc4;        // space-charge field per PIC cell: [cell][0] = (E_r, E_z) at its lower
+                               // nodes (i, j), (i+1, j), [cell][1] at (i, j+1), (i+1, j+1); or NULL
     int pnr, pnz;
     float psr;                 // (pnr - 1) * 2^-30
     unsigned long long *dep_q; // charge grid the launch deposits its active packs into at the end, or NULL

@@ -748,6 +748,29 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
     return 3;
 }
 
+__global__ void __launch_bounds__(256) esc_cells_kernel(PicGeom G, const PicInst *insts)
+{
+    const PicInst &I = insts[blockIdx.z];
+    if (I.esc4 == nullptr) return;
+    const int cr = G.pnr - 1;
+    const int64_t n = (int64_t)cr * (G.pnz - 1);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % cr), j = (int)(e / cr);
+        const float2 *s = I.esc + (size_t)j * G.pnr + i;
+        const float2 e00 = s[0], e10 = s[1], e01 = s[G.pnr], e11 = s[G.pnr + 1];
+        I.esc4[2 * e] = make_float4(e00.x, e00.y, e10.x, e10.y);
+        I.esc4[2 * e + 1] = make_float4(e01.x, e01.y, e11.x, e11.y);
+    }
+}
+
+void launch_esc_cells(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+{
+    const int64_t nc = (int64_t)(G.pnr - 1) * (G.pnz - 1);
+    esc_cells_kernel<<<dim3((unsigned)std::min<int64_t>((nc + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(
+        G, d_insts);
+}
+
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
     const int64_t nn = (int64_t)G.pnr * G.pnz;

@@ -31,6 +31,8 @@ struct PicInst {
     float *hat;              // [Nu][M] transformed residual / correction
     float *d32;              // [M][Nu] correction
     float2 *esc;             // [pnz][pnr] (E_r, E_z)
+    float4 *esc4;            // [pnz-1][pnr-1][2] the same per cell, the four nodes of a cell in one
+                             // 32-byte sector for the step kernels' gather (FP32 instances) or NULL
     double *er64, *ez64;     // FP64 copies for the FP64 path (or NULL)
     double *red;             // [0] ||b||^2, [1] ||r||^2, [2] rel. residual, [3] iterations, [4..6] PCG scalars,
                              // [7] pass counter of a captured solve loop (first instance of a launch)
@@ -133,5 +135,7 @@ template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const
 
 // E_SCE by central differences of Phi.
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
+// E_SCE regrouped per cell (esc -> esc4) for the instances that have esc4.
+void launch_esc_cells(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 
 } // namespace mucite

@@ -151,18 +151,18 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     L.nsig = fb.y > 0.0f ? __fdividef(P.psig * fb.x, fb.y) : 0.0f;
     L.ux = fb.z * cx; L.uy = fb.z * cy; L.uz = fb.w;
     L.esr = L.esz = 0.0f;
-    if (P.esc != nullptr) {
+    if (P.esc4 != nullptr) {
         int pi0, pj0;
         float pr, pz;
         cell_r(rr * P.psr, P.pnr, pi0, pr);
         cell_z(zq, P.pnz, pj0, pz);
-        const float2 *e = P.esc + (size_t)pj0 * P.pnr + pi0;
-        const float2 e00 = __ldg(&e[0]), e10 = __ldg(&e[1]), e01 = __ldg(&e[P.pnr]),
-                     e11 = __ldg(&e[P.pnr + 1]);
+        // the cell's four nodes in one 32-byte sector
+        const float4 *e = P.esc4 + 2 * ((size_t)pj0 * (P.pnr - 1) + pi0);
+        const float4 lo = __ldg(&e[0]), hi = __ldg(&e[1]);
         const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
                     v11 = pr * pz;
-        L.esr = v00 * e00.x + v10 * e10.x + v01 * e01.x + v11 * e11.x;
-        L.esz = v00 * e00.y + v10 * e10.y + v01 * e01.y + v11 * e11.y;
+        L.esr = v00 * lo.x + v10 * lo.z + v01 * hi.x + v11 * hi.z;
+        L.esz = v00 * lo.y + v10 * lo.w + v01 * hi.y + v11 * hi.w;
     }
 }
 
