@@ -194,3 +194,43 @@ def test_captured_solve_loops_match_direct(mc, masked):
             assert abs(int(pg["iterations"]) - int(pd["iterations"])) <= 1
         assert pg["rel_residual"] <= 1e-6 and pd["rel_residual"] <= 1e-6
         assert np.abs(pd["phi"]).max() > 0.0
+
+
+def test_autotune_restores_space_charge_state(mc):
+    """With a PIC grid the tuner's trials run whole macro steps (charge,
+    solve, E_SCE); the snapshot restores the pool and the space-charge state
+    (charge, potential, nodal and per-cell E_SCE), so the run afterwards is
+    bit-exact with an untuned run."""
+    import torch
+
+    def ring(n, seed):
+        w = W.ring_stack(n_packs=n, n_steps=0, seed=seed, precision=0, nr=129, nz=513)
+        w.fields.pic = W.Grid(65, 257, w.fields.grid.R, w.fields.grid.z0, w.fields.grid.z1)
+        w.run.pic_interval = 10
+        w.source.weight = 1000
+        w.source.prefill_z0, w.source.prefill_z1, w.source.radius = 3e-3, 30e-3, 3.5e-3
+        return w
+
+    ws = [ring(2000, 31), ring(900, 32)]
+    outs = []
+    for tune in (False, True):
+        ctx = mc.Context(0, torch.cuda.Stream())
+        ctx.set_tuning(64, 128)
+        ctx.load_fields(ws[0].fields)
+        for i, w in enumerate(ws):
+            ctx.inject(i, w.ion, w.source, w.run)
+        ctx.step(-1, 105)
+        if tune:
+            t = ctx.autotune([0, 1], 200)
+            assert t["steps_per_launch"] == 64 and t["n_tried"] > 0  # the PIC interval sets the macro step
+        ctx.step(-1, 205)
+        outs.append(([download(ctx, i, w.source.n_initial) for i, w in enumerate(ws)],
+                     [ctx.pic_read(i) for i in range(2)]))
+        ctx.close()
+    (sa, pa), (sb, pb) = outs
+    for a, b in zip(sa, sb):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    for a, b in zip(pa, pb):
+        assert (a["Q"] == b["Q"]).all()
+        assert np.abs(a["phi"] - b["phi"]).max() <= 1e-12 * max(np.abs(a["phi"]).max(), 1e-30)
