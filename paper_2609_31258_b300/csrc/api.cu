@@ -629,7 +629,7 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
     // per tile, so blocks whose packs finish early free their SM slot.
     const int pers = ctx->persistent > 0 ? ctx->persistent : (chunk <= 16 ? 32 : 0);
     if (pers > 0) {
-        const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(ctx->threads, chunk, collide, extras)));
+        const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(grid_f32(ctx), ctx->threads, chunk, collide, extras)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
     }
     launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,

@@ -41,7 +41,7 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
                      int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
                      cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
-int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras);
+int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras);
 void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, double srf_half,
                      double srf_next, cudaStream_t s);
 // Eq. 1 limits of one instance: out (device) [0] max rate, [1] max |v|,

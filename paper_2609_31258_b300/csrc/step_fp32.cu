@@ -667,8 +667,8 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
 // threads / kFreeU threads per block over the same tiles).
 constexpr int kFreeU = 2;
 
-template <bool kCollide, bool kExtras>
-__global__ void __launch_bounds__(kCollide ? 256 : 128, kCollide ? 4 : 6)
+template <bool kCollide, bool kExtras, int kMinBlocks>
+__global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
     step_f32_kernel(GridF32 G, const InstF32 *insts,
                                                        const int32_t *tile_start, int n_inst,
                                                        int total_tiles, int nsteps)
@@ -726,6 +726,17 @@ __global__ void advance_clock_kernel(InstF32 *insts, int n_inst, int nsteps)
     if (i < n_inst) insts[i].step0 += nsteps;
 }
 
+// Register budget of the collision kernel: 64 per thread (4 blocks of 256
+// per SM) while the static node table stays in L2, 80 (3 blocks) when it is
+// larger (the paper-sized grid): its gathers then wait on HBM, and the wider
+// budget keeps all eight node loads of a gather in flight (5 % faster there,
+// 5.6 % slower in the 10-step launches of a 1e6-pack run with an L2-resident
+// table).
+static bool wide_gather(const GridF32 &G)
+{
+    return (size_t)G.nr * (size_t)G.nz * sizeof(NodeF) > ((size_t)64 << 20);
+}
+
 // kCollide: the collision code is compiled in; kExtras: dissociation (Eq. 7)
 // and the hybrid Langevin branch are compiled in.
 void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
@@ -734,16 +745,25 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
 {
     rf_table_kernel<<<n_inst, 128, 0, s>>>(d_insts, nsteps);
     const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
-    if (collide && extras)
-        step_f32_kernel<true, true><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+    const bool wide = wide_gather(G);
+    if (collide && extras && wide)
+        step_f32_kernel<true, true, 3><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
+                                                                   nsteps);
+    else if (collide && extras)
+        step_f32_kernel<true, true, 4><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
+                                                                   nsteps);
+    else if (collide && wide)
+        step_f32_kernel<true, false, 3><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
+                                                                    nsteps);
     else if (collide)
-        step_f32_kernel<true, false><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles, nsteps);
+        step_f32_kernel<true, false, 4><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
+                                                                    nsteps);
     else if (extras)
-        step_f32_kernel<false, true><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
-                                                                           total_tiles, nsteps);
+        step_f32_kernel<false, true, 6><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
+                                                                              total_tiles, nsteps);
     else
-        step_f32_kernel<false, false><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
-                                                                            total_tiles, nsteps);
+        step_f32_kernel<false, false, 6><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
+                                                                               total_tiles, nsteps);
 }
 
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)
@@ -751,18 +771,22 @@ void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t
     advance_clock_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(d_insts, n_inst, nsteps);
 }
 
-int step_f32_blocks_per_sm(int threads, int nsteps, bool collide, bool extras)
+int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras)
 {
     int b = 0;
     const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
+    const bool wide = wide_gather(G);
     if (collide && extras)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, true>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, wide ? step_f32_kernel<true, true, 3> : step_f32_kernel<true, true, 4>, threads, smem);
     else if (collide)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<true, false>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, wide ? step_f32_kernel<true, false, 3> : step_f32_kernel<true, false, 4>, threads, smem);
     else if (extras)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, true>, threads / kFreeU, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, true, 6>, threads / kFreeU, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false>, threads / kFreeU, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_kernel<false, false, 6>, threads / kFreeU,
+                                                      smem);
     return b;
 }
 
