@@ -330,7 +330,9 @@ mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
  * use_graphs != 0: when all stepped instances share the space-charge
  * schedule and the context stream is not the legacy default stream, one macro
  * step (PIC update, RF table, fused step, clock advance) is captured once as
- * a CUDA graph and replayed.
+ * a CUDA graph and replayed. In the replayed macro step the solve loops stop
+ * on the device at convergence, and the step launch deposits the charge of
+ * the next PIC update at its end (results identical to use_graphs == 0).
  * Errors: MUCITE_E_ARG (persistent_blocks_per_sm outside [0, 32]). */
 mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_sm, int use_graphs);
 
