@@ -253,9 +253,9 @@ def main():
     ap.add_argument("--pic-packs", type=int, default=1_000_000)
     ap.add_argument("--pic-steps", type=int, default=2000)
     ap.add_argument("--pic-direct", action="store_true",
-                    help="space-charge section without graph replay: the solves run their fixed pass "
-                         "sequence as separate launches (a profiler cannot see the kernels of graphs "
-                         "that hold device-controlled loops)")
+                    help="space-charge and sweep sections without graph replay: the solves run their "
+                         "fixed pass sequence as separate launches (a profiler cannot see the kernels of "
+                         "graphs that hold device-controlled loops)")
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
@@ -553,6 +553,8 @@ def _sweep(args, local, stream, dev):
     base = W.ring_stack(n_packs=1, n_steps=0)
     pts = W.sweep_points(args.sweep_instances)
     ctx = mucite.Context(local, stream)
+    if args.pic_direct:
+        ctx.set_launch_mode(0, False)
     ctx.load_fields(f)
     for i, pt in enumerate(pts):
         run = dataclasses.replace(base.run, v_rf=pt["v_rf"], dc_scale=pt["dc_scale"], p_scale=pt["p_scale"],
