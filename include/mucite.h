@@ -324,9 +324,9 @@ mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
  * separate processes, Supporting Information S6; here many instances share
  * one launch). persistent_blocks_per_sm > 0: a persistent launch of that many
  * blocks per SM (capped by occupancy) whose blocks stride over the tiles of
- * every instance (block b takes tiles b, b + grid, ...); 0: automatic, one
- * block per tile for launches of more than 16 micro steps and the
- * occupancy-sized persistent grid for shorter ones.
+ * every instance (block b takes tiles b, b + grid, ...); 0: automatic, the
+ * occupancy-sized persistent grid for collision-free launches of at most 16
+ * micro steps, one block per tile otherwise.
  * use_graphs != 0: when all stepped instances share the space-charge
  * schedule and the context stream is not the legacy default stream, one macro
  * step (PIC update, RF table, fused step, clock advance) is captured once as

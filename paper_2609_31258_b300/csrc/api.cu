@@ -625,9 +625,11 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
     int grid = total_tiles;
     // Launches of a few micro steps (streamed) default to an occupancy-sized
     // grid striding over the tiles, which spares every tile the block start
-    // (descriptor copy, barriers); long fused launches default to one block
-    // per tile, so blocks whose packs finish early free their SM slot.
-    const int pers = ctx->persistent > 0 ? ctx->persistent : (chunk <= 16 ? 32 : 0);
+    // (descriptor copy, barriers); long fused launches and launches with
+    // collisions default to one block per tile, so blocks whose packs finish
+    // early free their SM slot (with collisions a block's warps finish at
+    // different times: 4.5 % less time per step in 10-step launches).
+    const int pers = ctx->persistent > 0 ? ctx->persistent : (chunk <= 16 && !collide ? 32 : 0);
     if (pers > 0) {
         const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(grid_f32(ctx), ctx->threads, chunk, collide, extras)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
