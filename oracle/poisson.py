@@ -98,10 +98,11 @@ def residual(pic, Q, phi):
 
 
 def masked_matrix(pic, metal):
-    """Operator with Phi = 0 imposed at metal-mask nodes ("Zero perturbation
-    potential is imposed ... at metal mask nodes"): metal unknowns get the
-    identity row, and their coupling is removed from fluid rows (Phi_metal = 0
-    there). `metal` is a bool array [nz][nr]."""
+    """Operator with Phi = 0 imposed at metal-mask nodes (the space-charge
+    potential vanishes on the electrodes, as the Methods' PIC space-charge
+    section states): metal unknowns get the identity row, and their coupling
+    is removed from fluid rows (Phi_metal = 0 there). `metal` is a bool array
+    [nz][nr]."""
     A = fv_matrix(pic).tocsr()
     m = np.asarray(metal)[1:-1, :-1].reshape(-1).astype(bool)
     keep = sp.diags((~m).astype(np.float64))

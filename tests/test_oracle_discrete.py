@@ -156,3 +156,91 @@ def test_efield_from_phi():
     assert np.allclose(ez[1:-1], -(6.0 * zz[1:-1] + 7.0), rtol=1e-10)
     # one-sided at the edges
     assert np.allclose(ez[0], -(phi[1] - phi[0]) / g.dz)
+
+
+def _teff_by_quadrature(ion, eint_over_kb):
+    """T with E_int(T)/k_B = eint, E_int(T) = integral of Cv from 0 to T and
+    Cv/k_B = 3N min(1, c0 + c1 T), inverted by root finding on the
+    numerically integrated heat capacity (no closed form involved)."""
+    from scipy import integrate, optimize
+    n3 = 3.0 * ion.n_atoms
+    knee = (1.0 - ion.cv_c0) / ion.cv_c1 if ion.cv_c1 > 0 else math.inf
+
+    def E(T):
+        pts = [knee] if 0.0 < knee < T else None
+        return integrate.quad(lambda t: n3 * min(1.0, ion.cv_c0 + ion.cv_c1 * t), 0.0, T, points=pts,
+                              epsabs=0.0, epsrel=1e-13, limit=200)[0]
+
+    return np.array([optimize.brentq(lambda T: E(T) - e, 0.0, 1e5, xtol=1e-12, rtol=1e-14) for e in eint_over_kb])
+
+
+def _bins_fp64(x, n):
+    """floor(x * n) clamped to [0, n-1], with a flag for values within 1e-6
+    (relative to one bin) of a bin edge, where the FP32/FP64 decision of the
+    oracle may fall on either side."""
+    y = np.asarray(x, np.float64) * n
+    b = np.clip(np.floor(y), 0, n - 1).astype(np.int64)
+    near = np.abs(y - np.rint(y)) < 1e-6
+    return b, near
+
+
+def test_tally_histogram_bins_recounted(orc):
+    """Every bin of the exit-radius, KE, T_eff and loss-map histograms,
+    recounted from the physical definitions in FP64: r in [0, r_det) over
+    n_r bins, KE = M v^2 / 2 in [0, ke_max) eV, T_eff (the temperature whose
+    integrated heat capacity is E_int) in [0, teff_max), and the loss map
+    over r in [0, R) x z in [z0, z1); values beyond the range land in the last
+    bin. A wrong bin scale, offset or axis swap fails here even though the
+    totals are unchanged (Eq. 8 and the terminal-event observables of the
+    Methods' terminal-events section)."""
+    w, s = _ring_sim(orc)
+    g, run, ion = w.fields.grid, w.run, w.ion
+    rng = np.random.default_rng(11)
+    n = 4000
+    st = rng.choice([1, 2], n, p=[0.6, 0.4]).astype(np.uint8)
+    # radius: transmitted packs over [0, 1.15 r_det], electrode hits over [0, R)
+    r = np.where(st == 1, rng.uniform(0, 1.15 * run.r_det, n), rng.uniform(0, 0.999 * g.R, n))
+    th = rng.uniform(0, 2 * math.pi, n)
+    xq = np.rint(r * np.cos(th) / g.R * S30).astype(np.int32)
+    yq = np.rint(r * np.sin(th) / g.R * S30).astype(np.int32)
+    zq = rng.integers(0, S30, n).astype(np.int32)
+    M = ion.mass_da * W.DALTON
+    ke = rng.uniform(0, 1.15 * run.ke_max_ev, n)
+    sp = np.sqrt(2.0 * ke * W.E_CHARGE / M)
+    u = rng.normal(size=(3, n))
+    u /= np.linalg.norm(u, axis=0)
+    v = sp * u
+    e = rng.uniform(0.0, 1.2 * 3.0 * ion.n_atoms * (run.teff_max - 350.0), n)
+    tt = rng.integers(0, 80000, n).astype(np.int32)
+    W_ = 7
+    w.source.weight = W_
+    T = s.tally(xq, yq, zq, v[0], v[1], v[2], e, st, tt)
+
+    tr, lo = st == 1, st == 2
+    r_lat = np.hypot(xq.astype(np.float64), yq.astype(np.float64)) * g.R / S30  # radius the lattice encodes
+    ke_v = 0.5 * M * (v ** 2).sum(0) / W.E_CHARGE
+    te = _teff_by_quadrature(ion, e[tr])
+    checks = [("r_hist", r_lat[tr] / run.r_det, run.n_r_bins),
+              ("ke_hist", ke_v[tr] / run.ke_max_ev, run.n_ke_bins),
+              ("teff_hist", te / run.teff_max, run.n_teff_bins)]
+    for name, x, nb in checks:
+        b, near = _bins_fp64(x, nb)
+        ref = np.bincount(b, minlength=nb) * W_
+        got = T[name]
+        assert got.sum() == ref.sum() == W_ * tr.sum(), name
+        if not near.any():
+            assert (got == ref).all(), (name, np.nonzero(got != ref)[0][:8])
+        else:  # a value on an edge may fall on either side
+            assert np.abs(got - ref).sum() <= 2 * W_ * near.sum(), name
+        assert (np.bincount(b, minlength=nb) > 0).sum() >= nb - 1, name  # every bin exercised
+    br, nr_ = _bins_fp64(r_lat[lo] / g.R, run.n_loss_r)
+    zf = zq[lo].astype(np.float64) / S30  # (z - z0) / (z1 - z0) on the lattice
+    bz, nz_ = _bins_fp64(zf, run.n_loss_z)
+    ref = np.zeros(run.n_loss_z * run.n_loss_r, np.int64)
+    np.add.at(ref, bz * run.n_loss_r + br, W_)
+    near = nr_ | nz_
+    got = np.asarray(T["loss_map"]).reshape(-1)  # [z bin][r bin]
+    assert got.sum() == ref.sum()
+    assert np.abs(got - ref).sum() <= 2 * W_ * near.sum()
+    if not near.any():
+        assert (got == ref).all()

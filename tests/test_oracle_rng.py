@@ -1,8 +1,9 @@
 """Pins of the oracle's counter-based generator and samplers.
 
-No known-answer vectors of Philox are available offline, so the generator is
-pinned by properties any correct Philox4x32-10 has: uniform 32-bit output,
-strong avalanche on single counter/key bit flips, and no correlation between
+Known answers for the generator come from test_oracle_philox_kat.py (an
+independent open-source Philox4x32-10); here it is also checked for the
+properties any correct Philox4x32-10 has: uniform 32-bit output, strong
+avalanche on single counter/key bit flips, and no correlation between
 neighbouring counters. The samplers are pinned by their distributions."""
 import math
 
