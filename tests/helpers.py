@@ -78,3 +78,49 @@ def binomial_band(k_a, k_b, n, nsig=3.0):
     p = 0.5 * (k_a + k_b) / n
     sd = math.sqrt(max(p * (1 - p), 1.0 / n) / n)
     return abs(k_a - k_b) / n <= nsig * sd
+
+
+def ensemble_stats(orc, ion, got, n_g, sim, n_o, labels=(1, 2, 3, 4)):
+    """The stochastic-ensemble criteria of the method's parity bar for a GPU
+    population `got` (downloaded pool, n_g packs) against an oracle
+    population `sim` (n_o packs): per terminal label the fractions, their
+    difference in standard deviations of a two-sample binomial proportion;
+    two-sample KS statistic and p-value on the kinetic energy and T_eff of
+    the packs still active; mean-T_eff ratio."""
+    from scipy import stats
+    m = ion.mass_da * 1.66053906660e-27
+    st_g, st_o = got["status"][:n_g], sim.status[:n_o]
+    out = {"labels": {}}
+    for lab in labels:
+        kg, ko = int((st_g == lab).sum()), int((st_o == lab).sum())
+        pg, po = kg / n_g, ko / n_o
+        p = (kg + ko) / (n_g + n_o)
+        sd = math.sqrt(max(p * (1 - p), 1.0 / (n_g + n_o)) * (1.0 / n_g + 1.0 / n_o))
+        out["labels"][int(lab)] = {"gpu": pg, "oracle": po, "sigma": abs(pg - po) / sd}
+    a_g, a_o = st_g == 0, st_o == 0
+    ke_g = 0.5 * m * (got["vx"][:n_g][a_g].astype(np.float64) ** 2 + got["vy"][:n_g][a_g].astype(np.float64) ** 2
+                      + got["vz"][:n_g][a_g].astype(np.float64) ** 2)
+    ke_o = 0.5 * m * (sim.vx[:n_o][a_o] ** 2 + sim.vy[:n_o][a_o] ** 2 + sim.vz[:n_o][a_o] ** 2)
+    ks = stats.ks_2samp(ke_g, ke_o)
+    out["ke_ks"] = {"D": float(ks.statistic), "p": float(ks.pvalue)}
+    T_of = np.vectorize(lambda e: orc.T_of_eint(ion, float(e)))
+    # T_eff of at most 200,000 packs per side (evenly strided) keeps the host work short
+    sg = max(1, int(a_g.sum()) // 200_000)
+    so = max(1, int(a_o.sum()) // 200_000)
+    T_g = T_of(got["eint"][:n_g][a_g][::sg].astype(np.float64))
+    T_o = T_of(sim.eint[:n_o][a_o][::so])
+    ks = stats.ks_2samp(T_g, T_o)
+    out["teff_ks"] = {"D": float(ks.statistic), "p": float(ks.pvalue)}
+    out["mean_teff_ratio"] = float(T_g.mean() / T_o.mean())
+    out["active"] = {"gpu": int(a_g.sum()), "oracle": int(a_o.sum())}
+    return out
+
+
+def assert_ensemble_bar(es):
+    """3-sigma binomial band per label, KS p > 0.01 on KE and T_eff, mean
+    T_eff within 0.5 %."""
+    for lab, v in es["labels"].items():
+        assert v["sigma"] <= 3.0, (lab, v)
+    assert es["ke_ks"]["p"] > 0.01, es["ke_ks"]
+    assert es["teff_ks"]["p"] > 0.01, es["teff_ks"]
+    assert abs(es["mean_teff_ratio"] - 1.0) < 0.005, es["mean_teff_ratio"]

@@ -70,6 +70,10 @@ def test_space_charge_full_size_deposit_and_solve(orc):
     Q = s.deposit()
     assert (got["Q"] == Q).all()
     assert Q.sum() == n * w.source.weight * 2 ** 30
-    assert got["rel_residual"] <= 1e-6
-    assert poisson.residual(w.fields.pic, Q, got["phi"]) <= 2e-6
+    # the paper's Poisson tolerance (Table S2: rtol 1e-6), on the residual the
+    # library reports and on the oracle's own recomputation of it from the
+    # returned potential; the two are the same quantity in FP64
+    res = poisson.residual(w.fields.pic, Q, got["phi"])
+    assert got["rel_residual"] <= 1e-6 and res <= 1e-6, (got["rel_residual"], res)
+    assert abs(res - got["rel_residual"]) <= 1e-3 * res + 1e-12, (got["rel_residual"], res)
     ctx.close()

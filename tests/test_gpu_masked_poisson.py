@@ -34,8 +34,13 @@ def test_masked_poisson_matches_direct(orc, pic_shape):
     metal = poisson.pic_metal_from_static(w.fields.grid, w.fields.mask, w.fields.pic)
     assert metal.any() and (~metal).any()
     ref = poisson.solve_masked(w.fields.pic, Q, metal)
+    # Table S2 tolerance (rtol 1e-6) on the reported residual and on the
+    # oracle's recomputation from the returned potential; PCG reports its
+    # recurrence residual, which tracks b - A_m Phi to FP64 rounding
+    res = poisson.residual_masked(w.fields.pic, Q, got["phi"], metal)
     assert got["rel_residual"] <= 1e-6 and got["iterations"] < 100
-    assert poisson.residual_masked(w.fields.pic, Q, got["phi"], metal) <= 2e-6
+    assert res <= 1e-6, (got["rel_residual"], res)
+    assert abs(res - got["rel_residual"]) <= 1e-3 * res + 1e-10, (got["rel_residual"], res)
     assert (got["phi"][metal] == 0.0).all()
     assert np.abs(got["phi"] - ref).max() <= 1e-4 * np.abs(ref).max()
     # the metal changes the answer: the maskless solve is far from it
