@@ -10,6 +10,9 @@
 // device array of fixed size, MUCITE_NOALLOC_SCRATCH_BYTES, that every device
 // which loads the library holds until the process exits. The caller passes
 // the node charges and the output buffers; nothing is allocated on any call.
+// The sine matrix and the tridiagonal factors depend on the grid only: they
+// are rebuilt when a call's grid differs from the one they were last built
+// for on that device.
 #include <mutex>
 
 #include "pic.cuh"
@@ -24,10 +27,22 @@ static __device__ __align__(256) unsigned char g_scratch[MUCITE_NOALLOC_SCRATCH_
 
 std::mutex g_setup_mutex;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
+int g_n_sm[kMaxDevices] = {};
+
+// Grid whose tables the scratch of a device holds (guarded by g_setup_mutex).
+struct TableKey {
+    int nr = 0, nz = 0;
+    double R = 0.0, z0 = 0.0, z1 = 0.0;
+    bool operator==(const TableKey &o) const
+    {
+        return nr == o.nr && nz == o.nz && R == o.R && z0 == o.z0 && z1 == o.z1;
+    }
+};
+TableKey g_tables[kMaxDevices];
 
 // Byte layout of the scratch for an M x Nu problem (256-byte aligned pieces).
 struct ScratchLayout {
-    size_t inst, red, conv, S, cp, invm, lo, a, c, A, r32, hat, d32, total;
+    size_t inst, red, conv, part, ticket, S, cp, invm, lo, a, c, A, r32, hat, d32, total;
 };
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -43,6 +58,8 @@ ScratchLayout scratch_layout(int M, int Nu)
     put(L.inst, sizeof(PicInst));
     put(L.red, 4 * sizeof(double));
     put(L.conv, sizeof(int));
+    put(L.part, 2 * (size_t)kRedBlocks * sizeof(double));
+    put(L.ticket, sizeof(unsigned));
     put(L.S, (size_t)M * M * sizeof(float));
     put(L.cp, (size_t)Nu * M * sizeof(float));
     put(L.invm, (size_t)Nu * M * sizeof(float));
@@ -132,20 +149,33 @@ extern "C" mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_str
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return MUCITE_E_CUDA;
     mucite_status st = MUCITE_OK;
     do {
+        // an error left by unrelated earlier work is not this call's
+        (void)cudaGetLastError();
         // One-time set-up on this device, with the device current: the host
         // name of the array is only a stand-in, so take its device address.
+        // Under lazy module loading this lookup is also what loads the module
+        // and reserves the array on the device.
         unsigned char *base = nullptr;
+        int n_sm = 0;
+        bool rebuild = false;
+        const TableKey key{pic->nr, pic->nz, pic->R, pic->z0, pic->z1};
         {
             std::lock_guard<std::mutex> lock(g_setup_mutex);
             if (!g_scratch_addr[device]) {
                 void *p = nullptr;
-                if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
+                int sms = 0;
+                if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess ||
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
                     st = MUCITE_E_CUDA;
                     break;
                 }
                 g_scratch_addr[device] = (unsigned char *)p;
+                g_n_sm[device] = sms;
             }
             base = g_scratch_addr[device];
+            n_sm = g_n_sm[device];
+            rebuild = !(g_tables[device] == key);
+            g_tables[device] = key; // the tables below are enqueued before any later call's work
         }
         cudaStream_t s = (cudaStream_t)cuda_stream;
         PicGeom G{};
@@ -163,13 +193,16 @@ extern "C" mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_str
         G.a = (double *)(base + L.a);
         G.c = (double *)(base + L.c);
         G.A = (double *)(base + L.A);
-        const double rz = (G.dr * G.dr) / (G.dz * G.dz);
-        const int64_t nt = std::max<int64_t>((int64_t)M * M, Nu);
-        na_tables_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(M, Nu, rz, (float *)G.S, (float *)G.lo,
-                                                                     (double *)G.a, (double *)G.c,
-                                                                     (double *)G.A);
-        na_thomas_factors_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, Nu, G.a, G.c, G.A, (float *)G.cp,
-                                                               (float *)G.invm);
+        G.n_sm = n_sm;
+        if (rebuild) {
+            const double rz = (G.dr * G.dr) / (G.dz * G.dz);
+            const int64_t nt = std::max<int64_t>((int64_t)M * M, Nu);
+            na_tables_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(M, Nu, rz, (float *)G.S,
+                                                                         (float *)G.lo, (double *)G.a,
+                                                                         (double *)G.c, (double *)G.A);
+            na_thomas_factors_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, Nu, G.a, G.c, G.A, (float *)G.cp,
+                                                                   (float *)G.invm);
+        }
         PicInst I{};
         I.Q = (unsigned long long *)d_Q;
         I.phi = d_phi;
@@ -181,12 +214,17 @@ extern "C" mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_str
         I.ez64 = nullptr;
         I.red = (double *)(base + L.red);
         I.conv = (int *)(base + L.conv);
+        // per-block partial sums added up in block order: the norms, the
+        // convergence decision and the reported residual are reproducible
+        I.part = (double *)(base + L.part);
+        I.ticket = (unsigned *)(base + L.ticket);
         PicInst *d_inst = (PicInst *)(base + L.inst);
         na_set_inst_kernel<<<1, 32, 0, s>>>(d_inst, I);
         // the solve starts from Phi = 0; bookkeeping left by the previous call is cleared
         if (cudaMemsetAsync(d_phi, 0, (size_t)pic->nr * pic->nz * sizeof(double), s) != cudaSuccess ||
             cudaMemsetAsync(I.red, 0, 4 * sizeof(double), s) != cudaSuccess ||
-            cudaMemsetAsync(I.conv, 0, sizeof(int), s) != cudaSuccess) {
+            cudaMemsetAsync(I.conv, 0, sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(I.ticket, 0, sizeof(unsigned), s) != cudaSuccess) {
             st = MUCITE_E_CUDA;
             break;
         }
@@ -194,6 +232,10 @@ extern "C" mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_str
         if (d_rel_residual) na_copy_rel_kernel<<<1, 32, 0, s>>>(I.red, d_rel_residual);
         if (cudaGetLastError() != cudaSuccess) st = MUCITE_E_CUDA;
     } while (0);
+    if (st != MUCITE_OK) {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        g_tables[device] = TableKey{}; // the tables may not have been built
+    }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     return st;
 }

@@ -16,14 +16,19 @@ from helpers import fp32_state_from_oracle, upload
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_solve_matches_pic_update_twice(orc):
+# 65 x 257: shared-memory Thomas sweeps; 150 x 257: cyclic reduction; 256 x
+# 1024 (the largest size the scratch holds, the benchmark's grid): cyclic
+# reduction and the DST-I contractions split over an 8-CTA cluster
+@pytest.mark.parametrize("shape", [(65, 257), (150, 257), (256, 1024)])
+def test_noalloc_solve_matches_pic_update_twice(orc, shape):
     import torch
     from paper_2609_31258_b300 import build, mucite
     build.build()
     pic = None
     stream = torch.cuda.current_stream(0)
+    pnr, pnz = shape
     for call, seed in enumerate((2, 9)):
-        w = W.cylinder_space_charge(n_packs=20000, n_steps=0, seed=seed, precision=0, pic_nr=65, pic_nz=257)
+        w = W.cylinder_space_charge(n_packs=20000, n_steps=0, seed=seed, precision=0, pic_nr=pnr, pic_nz=pnz)
         if call == 1:
             w.source.sigma, w.source.radius = 0.6e-3, 1.5e-3  # a different charge cloud
         pic = w.fields.pic
@@ -43,6 +48,14 @@ def test_noalloc_solve_matches_pic_update_twice(orc):
         torch.cuda.synchronize()
         phi, esc, rel = phi.cpu().numpy(), esc.cpu().numpy(), float(rel.item())
         assert rel <= 1e-6
+        # norms added up in block order: the same charges give the same
+        # potential and residual bit for bit on a repeated call
+        phi2 = torch.empty((pic.nz, pic.nr), dtype=torch.float64, device="cuda:0")
+        esc2 = torch.empty((pic.nz, pic.nr, 2), dtype=torch.float32, device="cuda:0")
+        rel2 = torch.empty((1,), dtype=torch.float64, device="cuda:0")
+        mucite.poisson_solve_noalloc(0, stream, pic, Q, phi2, esc2, rel2)
+        torch.cuda.synchronize()
+        assert (phi2.cpu().numpy() == phi).all() and float(rel2.item()) == rel
         assert np.abs(phi - ref["phi"]).max() <= 1e-4 * np.abs(ref["phi"]).max()
         scale = max(np.abs(ref["er"]).max(), np.abs(ref["ez"]).max())
         assert np.abs(esc[..., 0] - ref["er"]).max() <= 1e-3 * scale
