@@ -339,6 +339,14 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 /* Number of kernels this context has launched since creation. */
 int64_t mucite_launch_count(const mucite_ctx *ctx);
 
+/* CUDA-graph use of this context since creation (no counterpart in the
+ * paper; evidence of how the batched launches were issued): `replays` (out,
+ * may be NULL) the macro-step graphs launched, `captures` (out, may be NULL)
+ * the macro-step graphs captured and instantiated (a new one each time the
+ * stepped set of instances, their slot counts or the launch shape changes).
+ * Errors: MUCITE_E_ARG (ctx NULL). */
+mucite_status mucite_graph_stats(const mucite_ctx *ctx, int64_t *replays, int64_t *captures);
+
 /* Wait for all work enqueued on the context's stream. */
 mucite_status mucite_sync(mucite_ctx *ctx);
 
@@ -346,14 +354,14 @@ mucite_status mucite_sync(mucite_ctx *ctx);
 #define MUCITE_NOALLOC_SCRATCH_BYTES (10u * 1024u * 1024u)
 
 /* Space-charge Poisson solve that allocates nothing (the paper has no
- * counterpart; it is a deployment variant of the solve inside
+ * counterpart; it is a deployment variant of the maskless solve inside
  * mucite_pic_update).
  * Some callers cannot call cudaMalloc: processes whose device memory is fully
  * reserved up front (a serving process, or a host framework whose own pool
  * owns the device and forbids allocations outside it) and real-time loops
  * that must not block on the allocator. This entry point keeps all of its
  * scratch (sine matrix, tridiagonal factors, residual and transform buffers,
- * convergence flags) in one file-scope device array of
+ * block partial sums, convergence flags) in one file-scope device array of
  * MUCITE_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
  * until the process exits; it calls no allocator on any call.
  * Arguments: `device` is the CUDA device to run on (made current for the
@@ -363,11 +371,20 @@ mucite_status mucite_sync(mucite_ctx *ctx);
  * library); `d_phi` device FP64 [nz][nr] (output; the solve starts from
  * Phi = 0 on every call, boundary nodes are 0); `d_esc` device float
  * [nz][nr][2] (output E_r, E_z); `d_rel_residual` device double (output, may be
- * NULL): the final ||b - A Phi|| / ||b||. Same operator, FP32 DST-I +
- * tridiagonal correction, FP64 refinement to 1e-6 (at most 8 refinements) and
- * E differencing as mucite_pic_update. All work is enqueued on the stream.
+ * NULL): the final ||b - A Phi|| / ||b||. The operator is the maskless one of
+ * mucite_pic_update (Phi = 0 at both axial ends and at r = R only; metal
+ * nodes inside the grid are not imposed, unlike a run with pic_masked set):
+ * FP32 DST-I + tridiagonal correction, FP64 refinement to 1e-6 (at most 8
+ * refinements, norms added up in block order, so the result is reproducible)
+ * and E differencing. All work is enqueued on the stream.
  * Set-up: the first call on a device looks up the device address of the
- * scratch array; make that first call before any stream capture.
+ * scratch array and the device's SM count. Under CUDA's default lazy module
+ * loading that first call is also what loads the module and reserves the
+ * array's MUCITE_NOALLOC_SCRATCH_BYTES on the device, so it can fail with
+ * MUCITE_E_CUDA once the device memory is fully reserved: make the first call
+ * at start-up, before the memory budget is taken and before any stream
+ * capture. The sine matrix and the tridiagonal factors are rebuilt only when
+ * the grid differs from the previous call's on that device.
  * Every call shares the one scratch array, which keeps the last call's
  * contents (this call clears what it needs cleared): calls on the same device
  * that overlap on the GPU (different streams, or other host threads) race and

@@ -78,6 +78,7 @@ struct mucite_ctx {
     int persistent = 0;          // blocks per SM of a persistent launch, 0 = one block per tile
     int use_graphs = 1;
     int64_t launches = 0;
+    int64_t graph_replays = 0, graph_captures = 0;
     // captured macro step of the last group (replayed while the group is unchanged)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
@@ -722,10 +723,12 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 }
                 ctx->graph_key = key;
                 ctx->graph_launches = l;
+                ctx->graph_captures += 1;
             }
             for (int64_t r = 0; r < reps; ++r) {
                 CK(cudaGraphLaunch(ctx->graph, ctx->stream));
                 ctx->launches += ctx->graph_launches;
+                ctx->graph_replays += 1;
             }
             for (Instance *I : grp) I->step += reps * chunk;
             done += reps * chunk;
@@ -1598,6 +1601,14 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 }
 
 int64_t mucite_launch_count(const mucite_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+mucite_status mucite_graph_stats(const mucite_ctx *ctx, int64_t *replays, int64_t *captures)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (replays) *replays = ctx->graph_replays;
+    if (captures) *captures = ctx->graph_captures;
+    return MUCITE_OK;
+}
 
 mucite_status mucite_sync(mucite_ctx *ctx)
 {

@@ -25,7 +25,7 @@ EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_
            "mucite_step_set", "mucite_autotune",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
-           "mucite_dt_limits"]
+           "mucite_dt_limits", "mucite_graph_stats"]
 
 
 class MuciteError(RuntimeError):
@@ -122,6 +122,7 @@ def lib():
         L.mucite_launch_count.argtypes = [vp]
         L.mucite_launch_count.restype = C.c_int64
         L.mucite_sync.argtypes = [vp]
+        L.mucite_graph_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.mucite_poisson_solve_noalloc.argtypes = [C.c_int, vp, C.POINTER(Grid), vp, vp, vp, vp]
         L.mucite_set_dt.argtypes = [vp, C.c_int, C.c_double]
         L.mucite_dt_limits.argtypes = [vp, C.c_int, dp]
@@ -306,6 +307,12 @@ class Context:
 
     def sync(self):
         self._check(lib().mucite_sync(self._p))
+
+    def graph_stats(self):
+        """(macro-step graphs replayed, graphs captured) since creation."""
+        r, c = C.c_int64(), C.c_int64()
+        self._check(lib().mucite_graph_stats(self._p, C.byref(r), C.byref(c)))
+        return int(r.value), int(c.value)
 
     # -- views of a pack pool -------------------------------------------------
     def state(self, instance):

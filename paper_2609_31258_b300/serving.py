@@ -20,6 +20,14 @@ small requests finish early without starving large ones.
 Every request keeps its own Philox key (its seed) and its own clock, and
 per-pack arithmetic does not depend on the other packs of a launch, so a
 request's result is the same alone and in any mix, under either policy.
+
+Launches: a chunk advances the selected requests by `chunk` micro steps in
+one mucite_step_set call; with the context on a non-default stream and a
+chunk of at least two launches, the library captures the batched macro step
+as a CUDA graph once per selection and replays it. Back-pressure: the host
+enqueues at most `max_ahead` chunks ahead of the device (it waits for the
+event of an older chunk before enqueuing a new one), so admission and batch
+decisions are taken against the device's progress, not ahead of it.
 """
 from __future__ import annotations
 
@@ -76,11 +84,12 @@ def srpt_batch(active, clock, min_packs, waited=None, max_defer=None):
 
 
 class Server:
-    def __init__(self, ctx: mucite.Context, max_slots=32, chunk=2000, mem_reserve=2 << 30, policy="srpt",
-                 min_packs=None, max_defer=5.0):
+    def __init__(self, ctx: mucite.Context, max_slots=32, chunk=4000, mem_reserve=2 << 30, policy="srpt",
+                 min_packs=None, max_defer=5.0, max_ahead=2):
         self.ctx = ctx
         self.max_slots = min(max_slots, mucite.MAX_INSTANCES)
         self.chunk = chunk
+        self.max_ahead = max(1, int(max_ahead))
         self.mem_reserve = mem_reserve
         if policy not in ("all", "srpt"):
             raise ValueError(f"unknown batch policy {policy!r}")
@@ -121,8 +130,11 @@ class Server:
         return req
 
     def run(self, requests: List[Request], t_limit: Optional[float] = None):
+        import torch
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         done = []
+        inflight = deque()
+        stream = self.ctx.stream if self.ctx.stream is not None else torch.cuda.current_stream(self.ctx.device)
         t0 = time.perf_counter()
         while pending or self.active:
             now = time.perf_counter() - t0
@@ -141,7 +153,13 @@ class Server:
             else:
                 sel = sorted(self.active)
             step = min(self.chunk, min(self.active[s].n_steps - self.clock[s] for s in sel))
+            # back-pressure: at most max_ahead chunks queued on the device
+            while len(inflight) >= self.max_ahead:
+                inflight.popleft().synchronize()
             self.ctx.step_set(sel, step)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            inflight.append(ev)
             for s in sel:
                 self.clock[s] += step
                 self.last_step[s] = now

@@ -1,6 +1,9 @@
 """Continuous batching: requests arriving while others run are admitted into
 free slots and advanced together; every request's observables are the same
-as when it runs alone (integer tallies bit-exact, FP64 sums to rounding)."""
+as when it runs alone (integer tallies bit-exact, FP64 sums to rounding).
+The mix runs on a non-default stream, so its batched macro steps are
+captured as CUDA graphs and replayed; the requests run alone use direct
+launches on the default stream."""
 import numpy as np
 import pytest
 
@@ -11,20 +14,24 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("policy", ["all", "srpt"])
 def test_serving_mix_equals_alone(policy):
+    import torch
     from paper_2609_31258_b300 import build, mucite, serving
     build.build()
     base = W.ring_stack(n_packs=1, n_steps=0, nr=129, nz=513)
     base.run.z_exit = 7.0e-3  # short stack: some packs transmit within the run
     tmpl = W.SERVING_TEMPLATES
     spec = [(0.00, 3000, 0, 11), (0.01, 5000, 1, 12), (0.02, 700, 2, 13), (0.40, 2500, 0, 14), (0.41, 4096, 1, 15)]
-    ctx = mucite.Context(0)
+    ctx = mucite.Context(0, torch.cuda.Stream(torch.device("cuda", 0)))
     ctx.set_tuning(500, 128)
     ctx.load_fields(base.fields)
     reqs = [serving.make_request(i, t, n, tmpl[k], base, n_steps=3000, seed=sd)
             for i, (t, n, k, sd) in enumerate(spec)]
-    # srpt with a small fill: launches take subsets of the admitted requests
-    srv = serving.Server(ctx, max_slots=3, chunk=500, policy=policy, min_packs=4000, max_defer=0.5)
+    # srpt with a small fill: launches take subsets of the admitted requests;
+    # chunks of two 500-step launches are replayed from a captured graph
+    srv = serving.Server(ctx, max_slots=3, chunk=1000, policy=policy, min_packs=4000, max_defer=0.5)
     done, wall = srv.run(reqs)
+    replays, captures = ctx.graph_stats()
+    assert replays >= 2 * captures > 0
     assert len(done) == len(reqs)
     assert max(len(srv.active), 0) == 0
     lat = serving.latency_summary(done)
