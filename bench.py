@@ -192,6 +192,334 @@ def cpu_baseline_run(n_packs=100_000, min_seconds=10.0, max_micro=20000, w=None)
                       f"({ps} pack-steps in {dt:.1f} s, FP64 C oracle, OpenMP over packs)"}
 
 
+def cpu_baseline_rows():
+    """The oracle's pack-step rate on the three workloads of the CPU-baseline
+    plan, each on every host core and on one core: the tiny cylinder whole
+    (2,000 packs x 20,000 micro steps), the ring stack on a same-shape subset
+    (10,000 packs x 2,000 micro steps on the full 512 x 2048 fields) and the
+    space-charge cylinder on a subset (100,000 packs x 200 micro steps, PIC
+    256 x 1024 every 10 steps, the direct solve's factorisation included)."""
+    import oracle
+    from oracle import poisson
+    from paper_2609_31258_b300 import workloads as W
+    all_cores = os.cpu_count() or 1
+    jobs = [("tiny cylinder 64x256, whole (2000 packs x 20000 steps)",
+             lambda: W.tiny_cylinder(n_packs=2000, n_steps=0, precision=1), 20000, False),
+            ("ring stack 512x2048, subset (10000 packs x 2000 steps)",
+             lambda: W.ring_stack(n_packs=10_000, n_steps=0, precision=1), 2000, False),
+            ("cylinder + PIC 256x1024 every 10 steps, subset (100000 packs x 200 steps)",
+             lambda: W.cylinder_space_charge(n_packs=100_000, n_steps=0, precision=1), 200, True)]
+    rows = []
+    prev = oracle.threads()
+    try:
+        for cores in (all_cores, 1):
+            used = oracle.threads(cores)
+            for name, make, nsteps, pic in jobs:
+                w = make()
+                s = oracle.Sim(w, capacity=w.source.n_initial + 64)
+                s.inject()
+                poisson._cache.clear()
+                t0 = time.perf_counter()
+                if pic:
+                    s.advance(nsteps)
+                else:
+                    s.steps(nsteps)
+                dt = time.perf_counter() - t0
+                ps = int(s.nsteps[:s.n].sum())
+                rows.append({"workload": name, "cores": used, "value": ps / dt, "unit": UNIT, "seconds": dt})
+    finally:
+        oracle.threads(prev)
+    return rows
+
+
+# --------------------------------------------------------------------------
+# Error against the FP64 oracle, per output. The oracle runs of the CPU
+# baseline leg serve as the reference: the FP32 fused path and the plain
+# FP64 GPU path start from the oracle's state (same state, same seed) or run
+# their own injection with another seed (independent samples).
+# --------------------------------------------------------------------------
+_LAT = 2.0 ** 30
+
+
+def _to_fp32_state(sim):
+    """Lattice positions and FP32 velocity / E_int of the oracle's packs; the
+    oracle is reset to exactly those values so both sides start equal."""
+    import numpy as np
+    n, g = sim.n, sim.g
+    sx, sz = _LAT / g.R, _LAT / (g.z1 - g.z0)
+    xq = np.rint(sim.x[:n] * sx).astype(np.int32)
+    yq = np.rint(sim.y[:n] * sx).astype(np.int32)
+    zq = np.rint((sim.z[:n] - g.z0) * sz).astype(np.int32)
+    st = dict(x=xq, y=yq, z=zq, status=sim.status[:n].copy(), t_term=sim.t_term[:n].copy())
+    for k in ("vx", "vy", "vz", "eint", "lnsy", "tau"):
+        st[k] = getattr(sim, k)[:n].astype(np.float32)
+        getattr(sim, k)[:n] = st[k].astype(np.float64)
+    sim.x[:n] = xq.astype(np.float64) / sx
+    sim.y[:n] = yq.astype(np.float64) / sx
+    sim.z[:n] = g.z0 + zq.astype(np.float64) / sz
+    return st
+
+
+def _to_fp64_state(sim):
+    n = sim.n
+    return {k: getattr(sim, k)[:n].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "eint", "status", "t_term",
+                                                      "lnsy", "tau")}
+
+
+def _gpu_run(local, stream, w, state, nsteps, spl=2000):
+    """Run a workload on the library from an uploaded state (or from its own
+    injection when state is None); returns the pool as numpy and the
+    context (caller closes)."""
+    import numpy as np
+    import torch
+    from paper_2609_31258_b300 import mucite
+    ctx = mucite.Context(local, stream)
+    ctx.set_tuning(spl, 256)
+    mucite.load_workload(ctx, w, 0)
+    if state is not None:
+        views = ctx.state(0)
+        n = len(state["status"])
+        for k, a in state.items():
+            views[k][:n].copy_(torch.from_numpy(np.ascontiguousarray(a)))
+        torch.cuda.synchronize()
+        ctx.resume(0, n, 0)
+    if nsteps:
+        ctx.step(0, nsteps)
+    return _download(ctx), ctx
+
+
+def _download(ctx):
+    import torch
+    ctx.sync()
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in ctx.state(0).items()}
+
+
+def _pos_err(g, got, sim, n, lattice):
+    import numpy as np
+    if lattice:
+        gx = got["x"][:n].astype(np.float64) * g.R / _LAT
+        gy = got["y"][:n].astype(np.float64) * g.R / _LAT
+        gz = g.z0 + got["z"][:n].astype(np.float64) * (g.z1 - g.z0) / _LAT
+    else:
+        gx, gy, gz = got["x"][:n], got["y"][:n], got["z"][:n]
+    act = (got["status"][:n] == 0) & (sim.status[:n] == 0)
+    d = np.sqrt((gx - sim.x[:n]) ** 2 + (gy - sim.y[:n]) ** 2 + (gz - sim.z[:n]) ** 2)
+    nrm = np.sqrt(sim.x[:n] ** 2 + sim.y[:n] ** 2 + (sim.z[:n] - g.z0) ** 2)
+    e = (d / nrm)[act]
+    return {"max": float(e.max()) if e.size else None, "median": float(np.median(e)) if e.size else None,
+            "packs": int(act.sum())}
+
+
+def _ensemble(oracle, ion, got, n_g, sim, n_o):
+    """Per terminal label the fractions and their difference in standard
+    deviations of a two-sample binomial proportion; KS on KE and T_eff of
+    the active packs; mean-T_eff ratio (GPU / oracle)."""
+    import numpy as np
+    from scipy import stats
+    m = ion.mass_da * 1.66053906660e-27
+    st_g, st_o = got["status"][:n_g], sim.status[:n_o]
+    lab = {}
+    for k, name in ((1, "transmitted"), (2, "electrode"), (3, "radial"), (4, "axial")):
+        kg, ko = int((st_g == k).sum()), int((st_o == k).sum())
+        p = (kg + ko) / (n_g + n_o)
+        sd = math.sqrt(max(p * (1 - p), 1.0 / (n_g + n_o)) * (1.0 / n_g + 1.0 / n_o))
+        lab[name] = {"gpu": kg / n_g, "oracle": ko / n_o, "sigma": abs(kg / n_g - ko / n_o) / sd}
+    a_g, a_o = st_g == 0, st_o == 0
+    ke = lambda vx, vy, vz: 0.5 * m * (vx.astype(np.float64) ** 2 + vy.astype(np.float64) ** 2 +
+                                       vz.astype(np.float64) ** 2) / 1.602176634e-19
+    ke_g = ke(got["vx"][:n_g][a_g], got["vy"][:n_g][a_g], got["vz"][:n_g][a_g])
+    ke_o = ke(sim.vx[:n_o][a_o], sim.vy[:n_o][a_o], sim.vz[:n_o][a_o])
+    T_of = np.vectorize(lambda e: oracle.T_of_eint(ion, float(e)))
+    T_g = T_of(got["eint"][:n_g][a_g].astype(np.float64))
+    T_o = T_of(sim.eint[:n_o][a_o])
+    k1, k2 = stats.ks_2samp(ke_g, ke_o), stats.ks_2samp(T_g, T_o)
+    return {"labels": lab, "ke_ks": {"D": float(k1.statistic), "p": float(k1.pvalue)},
+            "teff_ks": {"D": float(k2.statistic), "p": float(k2.pvalue)},
+            "mean_ke_ratio": float(ke_g.mean() / ke_o.mean()), "mean_teff_ratio": float(T_g.mean() / T_o.mean())}
+
+
+def _pack_diffs(oracle, ion, got, sim, n):
+    """Same state, same seed: label agreement and per-pack relative
+    differences of KE and T_eff over the packs active on both sides."""
+    import numpy as np
+    agree = float((got["status"][:n] == sim.status[:n]).mean())
+    a = (got["status"][:n] == 0) & (sim.status[:n] == 0)
+    v2g = sum(got[k][:n][a].astype(np.float64) ** 2 for k in ("vx", "vy", "vz"))
+    v2o = sum(getattr(sim, k)[:n][a] ** 2 for k in ("vx", "vy", "vz"))
+    dke = np.abs(v2g / v2o - 1.0)
+    T_of = np.vectorize(lambda e: oracle.T_of_eint(ion, float(e)))
+    dT = np.abs(T_of(got["eint"][:n][a].astype(np.float64)) / T_of(sim.eint[:n][a]) - 1.0)
+    return {"label_agreement": agree, "ke_rel_median": float(np.median(dke)), "ke_rel_p99": float(np.quantile(dke, 0.99)),
+            "teff_rel_median": float(np.median(dT)), "teff_rel_p99": float(np.quantile(dT, 0.99))}
+
+
+def parity_report(local, stream):
+    """Error of the FP32 fused path and of the plain FP64 GPU path against
+    the FP64 oracle, per output, on bounded samples of the benchmarked
+    workloads (seconds of oracle work each)."""
+    import numpy as np
+    import oracle
+    from oracle import poisson
+    from paper_2609_31258_b300 import workloads as W
+    out = {}
+    t_start = time.perf_counter()
+
+    # collision-free trajectories on the full ring-stack fields: position
+    n = 10_000
+    w = W.ring_stack(n_packs=n, n_steps=0, seed=31, precision=0)
+    w.fields.gas_p[:] = 0.0
+    w.source.T_vel = 3000.0
+    s = oracle.Sim(w)
+    s.inject()
+    st32 = _to_fp32_state(s)
+    st64 = _to_fp64_state(s)
+    g32, c = _gpu_run(local, stream, w, st32, 4000)
+    c.close()
+    w.run.precision = 1
+    g64, c = _gpu_run(local, stream, w, st64, 4000)
+    c.close()
+    s.steps(4000)
+    g = w.fields.grid
+    out["position_collision_free"] = {
+        "workload": "ring stack 512x2048, no gas, 10000 packs at 3000 K, 4000 micro steps, same state",
+        "fp32": _pos_err(g, g32, s, n, True), "fp64_gpu": _pos_err(g, g64, s, n, False),
+        "label_agreement_fp32": float((g32["status"][:n] == s.status[:n]).mean()),
+        "label_agreement_fp64": float((g64["status"][:n] == s.status[:n]).mean()), "bar": "max < 1e-5"}
+
+    # collisions on the ring stack: KE, T_eff, collision rate
+    w = W.ring_stack(n_packs=n, n_steps=0, seed=1, precision=0)
+    s = oracle.Sim(w)
+    s.inject()
+    st32 = _to_fp32_state(s)
+    st64 = _to_fp64_state(s)
+    g32, c = _gpu_run(local, stream, w, st32, 2000)
+    T32 = c.tally(0)
+    c.close()
+    w.run.precision = 1
+    g64, c = _gpu_run(local, stream, w, st64, 2000)
+    c.close()
+    s.steps(2000)
+    w.run.precision = 0
+    gi, c = _gpu_run(local, stream, w, None, 2000)
+    c.close()
+    wo = W.ring_stack(n_packs=n, n_steps=0, seed=1001, precision=1)
+    so = oracle.Sim(wo)
+    so.inject()
+    so.steps(2000)
+    out["collisions_ring_stack"] = {
+        "workload": "ring stack 512x2048 with gas, 10000 packs, 2000 micro steps",
+        "same_state_fp32": _pack_diffs(oracle, w.ion, g32, s, n),
+        "same_state_fp64": _pack_diffs(oracle, w.ion, g64, s, n),
+        "collisions_per_pack_step": {"fp32": T32["collisions"] / max(T32["pack_steps"], 1),
+                                     "oracle": float(s.ncoll[:n].sum() / s.nsteps[:n].sum())},
+        "independent_seeds_fp32": _ensemble(oracle, w.ion, gi, n, so, n)}
+
+    # terminal labels and transmission on the tiny cylinder with a near exit
+    n = 10_000
+
+    def cyl(seed, prec):
+        w = W.tiny_cylinder(n_packs=n, n_steps=0, precision=prec, seed=seed)
+        w.run.z_exit, w.run.r_det = 0.6e-3, 0.8e-3
+        return w
+    w = cyl(4, 0)
+    s = oracle.Sim(w)
+    s.inject()
+    st32 = _to_fp32_state(s)
+    g32, c = _gpu_run(local, stream, w, st32, 12000)
+    c.close()
+    s.steps(12000)
+    gi, c = _gpu_run(local, stream, cyl(5, 0), None, 12000)
+    c.close()
+    so = oracle.Sim(cyl(1005, 1))
+    so.inject()
+    so.steps(12000)
+    out["labels_cylinder"] = {
+        "workload": "tiny cylinder 64x256, z_exit 0.6 mm, r_det 0.8 mm, 10000 packs, 12000 micro steps",
+        "same_state_fp32": _pack_diffs(oracle, w.ion, g32, s, n),
+        "independent_seeds_fp32": _ensemble(oracle, w.ion, gi, n, so, n)}
+
+    # ln SY (Eq. 7) of hot dissociating ions cooling in the gas
+    n = 3000
+
+    def tst(prec):
+        w = W.tiny_cylinder(n_packs=n, n_steps=0, precision=prec, seed=17)
+        w.fields.phi_dc[:] = 0.0
+        w.source.z_plane = 10e-3
+        w.ion = W.IonTemplate(mass_da=556.27, charge=1, ccs_m2=1.62e-18, n_atoms=77, T_init=1100.0,
+                              dH_kJmol=111.7, dS_JmolK=-38.1)
+        return w
+    w = tst(0)
+    s = oracle.Sim(w)
+    s.inject()
+    st32 = _to_fp32_state(s)
+    st64 = _to_fp64_state(s)
+    g32, c = _gpu_run(local, stream, w, st32, 4000, spl=500)
+    c.close()
+    g64, c = _gpu_run(local, stream, tst(1), st64, 4000, spl=500)
+    c.close()
+    s.steps(4000)
+    sy_o = np.exp(s.lnsy[:n])
+
+    def sy(got):
+        d = np.abs(got["lnsy"][:n].astype(np.float64) - s.lnsy[:n])
+        return {"mean_sy_ratio": float(np.exp(got["lnsy"][:n].astype(np.float64)).mean() / sy_o.mean()),
+                "ln_sy_abs_median": float(np.median(d)), "ln_sy_abs_p99": float(np.quantile(d, 0.99))}
+    out["survival_yield"] = {"workload": "tiny cylinder, 556 Da/+1 at 1100 K, dH 111.7 kJ/mol, dS -38.1 J/mol/K, "
+                                         "3000 packs, 4000 micro steps, same state",
+                             "mean_sy_oracle": float(sy_o.mean()), "fp32": sy(g32), "fp64_gpu": sy(g64)}
+
+    # space charge: deposit, potential, field, residual
+    n = 100_000
+    w = W.cylinder_space_charge(n_packs=n, n_steps=0, precision=0)
+    s = oracle.Sim(w)
+    s.inject()
+    st32 = _to_fp32_state(s)
+    st64 = _to_fp64_state(s)
+    Q, phi = s.pic_update()
+    pic = w.fields.pic
+    res = {}
+    for prec, st in ((0, st32), (1, st64)):
+        w.run.precision = prec
+        _, c = _gpu_run(local, stream, w, st, 0)
+        c.pic_update(0)
+        pr = c.pic_read(0)
+        c.close()
+        er, ez = oracle.efield_from_phi(phi, pic.dr, pic.dz)
+        d = {"deposit_mismatched_nodes": int((pr["Q"] != Q).sum()),
+             "phi_rel_max": float(np.abs(pr["phi"] - phi).max() / np.abs(phi).max()),
+             "rel_residual_reported": float(pr["rel_residual"]),
+             "rel_residual_recomputed": poisson.residual(pic, Q, pr["phi"]),
+             "solve_passes": int(pr["iterations"])}
+        scale = max(np.abs(er).max(), np.abs(ez).max())
+        d["esc_rel_max"] = float(max(np.abs(pr["er"] - er).max(), np.abs(pr["ez"] - ez).max()) / scale)
+        res["fp32" if prec == 0 else "fp64_gpu"] = d
+    out["space_charge"] = dict(workload="cylinder 1e5 packs prefilled, PIC 256x1024, one update, same state",
+                               **res)
+
+    # the space-charge run as an ensemble: independent seeds, 1e5 packs (with
+    # 1e6 the beam's own field couples the packs of a run through the noise
+    # of their charge grid and even oracle-vs-oracle fails an i.i.d. KS test)
+    def sc(seed, prec):
+        w = W.cylinder_space_charge(n_packs=n, n_steps=0, seed=seed, precision=prec)
+        w.source.current_A = 0.0
+        return w
+    w = sc(2, 0)
+    _, ctx = _gpu_run(local, stream, w, None, 0)
+    for _ in range(4):
+        ctx.step(0, 100)
+    gi = _download(ctx)
+    ctx.close()
+    so = oracle.Sim(sc(1002, 1))
+    so.inject()
+    so.advance(400)
+    out["space_charge_ensemble"] = {
+        "workload": "cylinder, 1e5 packs at W = 1e3, PIC 256x1024 every 10 steps, 400 micro steps, seeds 2 vs 1002",
+        "independent_seeds_fp32": _ensemble(oracle, w.ion, gi, n, so, n)}
+    out["seconds"] = time.perf_counter() - t_start
+    return out
+
+
 def _config(args, name, ws):
     """The workload, identical for both arms (the launch shape is reported
     separately by the CUDA arm)."""
@@ -238,18 +566,21 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true", help="keep 2000 steps per launch, 256-pack tiles")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 path")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle legs (CPU baseline, its per-workload rows and the parity report)")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-output error report")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--streamed-packs", type=int, default=8_000_000)
     ap.add_argument("--streamed-threads", type=int, default=256, help="packs per tile of the streamed launch")
     ap.add_argument("--streamed-persistent", type=int, default=0,
                     help="persistent blocks per SM of the streamed launch (0: one block per tile)")
-    ap.add_argument("--serve-requests", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=200, help="first arrivals served at 20 / s")
     ap.add_argument("--serve-steps", type=int, default=100_000, help="micro steps per request (50 us)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-pic", action="store_true")
+    ap.add_argument("--no-paper-grid", action="store_true")
     ap.add_argument("--pic-packs", type=int, default=1_000_000)
     ap.add_argument("--pic-steps", type=int, default=2000)
     ap.add_argument("--pic-direct", action="store_true",
@@ -259,8 +590,9 @@ def main():
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--sweep-tune-steps", type=int, default=200, help="autotuner trial length (0: no tuning)")
-    ap.add_argument("--serve-sustainable", type=int, default=-1,
-                    help="requests replayed at 70%% of capacity (-1: as many as --serve-requests, 0: skip)")
+    ap.add_argument("--serve-search-requests", type=int, default=24,
+                    help="arrivals served in each trial of the sustainable-rate search (0: no search)")
+    ap.add_argument("--serve-search-trials", type=int, default=3, help="most trials of the sustainable-rate search")
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
     ap.add_argument("--section", default="all",
@@ -363,13 +695,15 @@ def main():
     spl = args.spl or 2000
     step_launches = -(-args.micro // spl)
     kern_ms = t_ms / args.steps / step_launches
-    insts = _inst_per_pack_step()
+    prof, stale = _profile_fields()
+    insts = None if stale else float(prof["inst_per_pack_step"]) if "inst_per_pack_step" in prof else None
+    traffic = None if stale else float(prof["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in prof else None
     sm_mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     peak_ginst = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9  # lane-instructions/s, in G
     ps_per_launch = pack_steps / (args.steps * step_launches)
     ach = insts * ps_per_launch / (kern_ms * 1e-3) / 1e9 if insts else None
     roofline = {"bound": "alu", "achieved": ach, "peak": peak_ginst, "unit": "Ginst/s (thread instructions)",
-                "frac": (ach / peak_ginst) if ach else None, "traffic": _traffic_per_launch(),
+                "frac": (ach / peak_ginst) if ach else None, "traffic": traffic, "profile_stale": stale,
                 "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
                 "inst_per_pack_step": insts, "pack_steps_per_launch": ps_per_launch,
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
@@ -396,13 +730,22 @@ def main():
     space_charge = None
     if not args.no_pic:
         space_charge = _space_charge(args, local, stream, dev)
+    paper = None
+    if not args.no_paper_grid:
+        paper = _paper_grid(args, local, stream, dev)
     serve = None
     if not args.no_serving:
         serve = _serving(args, local)
 
-    cpu = None
+    # CPU-baseline leg (rank 0): the oracle timed on the host cores, its rows
+    # on the three planned workloads, and its runs as the reference of the
+    # per-output error report
+    cpu = parity = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_run()
+        cpu["rows"] = cpu_baseline_rows()
+        if not args.no_parity:
+            parity = parity_report(local, stream)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -417,7 +760,9 @@ def main():
                "streamed_push": streamed,
                "sweep": sweep,
                "space_charge": space_charge,
+               "paper_grid": paper,
                "serving": serve,
+               "parity": parity,
                "peaks_source": peak_src}
         print(json.dumps(out))
     ctx.close()
@@ -440,28 +785,50 @@ def aggregate(t_ms, pack_steps, dev, ws):
     return float(t.item()), float(p.item())
 
 
-def _inst_per_pack_step():
-    """Thread instructions per active pack-step of the fused kernel, from the
-    committed ncu summary (profiles/step_f32_ring_stack.txt)."""
-    p = os.path.join(ROOT, "profiles", "step_f32_ring_stack.txt")
-    try:
-        for ln in open(p):
-            if ln.startswith("inst_per_pack_step:"):
-                return float(ln.split(":")[1])
-    except OSError:
-        pass
-    return None
+def source_stamp(cu_name="step_fp32.cu"):
+    """SHA-256 of the code a kernel is compiled from: the CUDA source and its
+    local includes (transitively), comments and blank space removed, so a
+    profile summary taken on other code is recognised as stale."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2609_31258_b300", "csrc")
+    seen, order = set(), []
+
+    def visit(path):
+        path = os.path.normpath(path)
+        if path in seen or not os.path.exists(path):
+            return
+        seen.add(path)
+        src = open(path).read()
+        order.append((os.path.relpath(path, ROOT), src))
+        for inc in re.findall(r'#include\s+"([^"]+)"', src):
+            visit(os.path.join(os.path.dirname(path), inc))
+
+    visit(os.path.join(csrc, cu_name))
+    h = hashlib.sha256()
+    for rel, src in sorted(order):
+        code = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        code = "\n".join(ln.strip() for ln in code.splitlines() if ln.strip())
+        h.update(rel.encode() + b"\0" + code.encode() + b"\0")
+    return h.hexdigest()
 
 
-def _traffic_per_launch():
-    p = os.path.join(ROOT, "profiles", "step_f32_ring_stack.txt")
+def _profile_fields(name="step_f32_ring_stack.txt", cu_name="step_fp32.cu"):
+    """Figures of a committed ncu summary, and whether it was taken on the
+    code that is built now (its sources_sha256 line against source_stamp)."""
+    p = os.path.join(ROOT, "profiles", name)
+    out = {}
     try:
         for ln in open(p):
-            if ln.startswith("dram_bytes_per_launch:"):
-                return float(ln.split(":")[1])
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                out[k.strip()] = v.strip()
     except OSError:
-        pass
-    return None
+        return {}, "no profile summary"
+    if out.get("sources_sha256", "").split(" ")[0] != source_stamp(cu_name):
+        return out, f"profiles/{name} was taken on other {cu_name} sources: re-profile"
+    return out, None
 
 
 def _e2e(ctx, args, stream, dev):
@@ -651,48 +1018,97 @@ def _paper_grid(args, local, stream, dev):
     ctx.close()
     ms = a.elapsed_time(b)
     ps = T1["pack_steps"] - T0["pack_steps"]
+    # HBM roofline of the launch: DRAM bytes per launch from the committed
+    # ncu summary of the same launch (null once the kernel's sources change)
+    prof, stale = _profile_fields("step_f32_paper_grid.txt")
+    peak = _peaks()[0]["hbm_gbs"]
+    launch_ms = ms / args.steps
+    traffic = None if stale or "dram_bytes_per_launch" not in prof else float(prof["dram_bytes_per_launch"])
+    ach = traffic / (launch_ms * 1e-3) / 1e9 if traffic else None
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None,
+            "traffic": traffic, "kernel_ms_per_launch": launch_ms, "pack_steps_per_launch": ps / args.steps,
+            "dram_bytes_per_pack_step": traffic / (ps / args.steps) if traffic else None, "profile_stale": stale,
+            "note": "DRAM bytes of the node gathers (table not L2-resident) and of the pack state, per launch"}
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "grid": "2001x6501", "packs": args.packs,
-            "micro_steps": 2000 * args.steps, "ms": ms, "collisions_per_pack_step": (T1["collisions"] - T0["collisions"]) / max(ps, 1)}
+            "micro_steps": 2000 * args.steps, "ms": ms,
+            "collisions_per_pack_step": (T1["collisions"] - T0["collisions"]) / max(ps, 1), "roofline": roof}
 
 
 def _serving(args, local):
     """Serving loop on the ring-stack geometry: Poisson arrivals at 20 / s,
     pack counts log-uniform in [1e4, 2e6], three ion templates, 50 us
-    (1e5 micro steps) per request; the first --serve-requests arrivals. The
-    same requests are then replayed at a sustainable arrival rate (70 % of
-    the capacity measured in the first run), arrival times stretched."""
+    (1e5 micro steps) per request, the first --serve-requests arrivals
+    (default 200). The offered load exceeds the capacity at 20 / s, so the
+    latency there is queue dominated. Then the highest sustainable arrival
+    rate is searched on the first --serve-search-requests arrivals, their
+    arrival times stretched: starting just below the capacity the first run
+    measured, the rate is lowered until the latency stops growing with the
+    run (the mean latency of the last third of the requests within 1.5 x
+    that of the first third plus the requests' mean service time alone)."""
+    import numpy as np
     import torch
     from paper_2609_31258_b300 import mucite, serving, workloads as W
     base = W.ring_stack(n_packs=1, n_steps=0, precision=0)
     t, n, tmpl = W.serving_arrivals(n_req=args.serve_requests, rate_hz=20.0, seed=5)
+    dev = torch.device("cuda", local)
 
     def once(rate, count):
         arr = t * (20.0 / rate)
         reqs = [serving.make_request(i, arr[i], int(n[i]), W.SERVING_TEMPLATES[int(tmpl[i])], base,
                                      n_steps=args.serve_steps, seed=1000 + i) for i in range(count)]
-        ctx = mucite.Context(local)
+        # a non-default stream: the batched macro steps are graph-captured and replayed
+        ctx = mucite.Context(local, torch.cuda.Stream(dev))
         ctx.set_tuning(2000, 256)
         ctx.load_fields(base.fields)
-        srv = serving.Server(ctx, max_slots=64, chunk=2000, policy=args.serve_policy)
+        srv = serving.Server(ctx, max_slots=64, chunk=4000, policy=args.serve_policy)
         torch.cuda.synchronize()
         done, wall = srv.run(reqs)
+        replays, captures = ctx.graph_stats()
+        launches = ctx.launch_count()
         ctx.close()
         lat = serving.latency_summary(done)
         work = sum(r.tally["pack_steps"] for r in done)
+        by_arrival = sorted(done, key=lambda r: r.arrival)
+        third = max(1, len(by_arrival) // 3)
+        first = float(np.mean([r.latency for r in by_arrival[:third]]))
+        last = float(np.mean([r.latency for r in by_arrival[-third:]]))
         return {"requests": len(done), "arrival_rate_hz": rate, "policy": args.serve_policy,
                 "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"], "mean_latency_s": lat.get("mean_s"),
-                "wall_s": wall, "pack_steps": int(work), "throughput": work / wall, "unit": UNIT}
+                "mean_latency_first_third_s": first, "mean_latency_last_third_s": last,
+                "wall_s": wall, "pack_steps": int(work), "throughput": work / wall, "unit": UNIT,
+                "graph_replays": replays, "graph_captures": captures, "gpu_launches": launches}
 
     first = once(20.0, args.serve_requests)
     first.update({"micro_steps_per_request": args.serve_steps, "packs": [int(x) for x in n],
                   "templates": [int(x) for x in tmpl],
                   "note": "offered load exceeds capacity at 20 / s: latency is queue dominated"})
-    busy = first["wall_s"] - float(t[0])
-    capacity = len(n) / busy if busy > 0 else None
-    if capacity and args.serve_sustainable != 0:
-        sus = once(0.7 * capacity, args.serve_sustainable if args.serve_sustainable > 0 else len(n))
-        sus["note"] = "same requests, arrivals stretched to 70 % of the capacity measured at 20 / s"
-        first["sustainable"] = sus
+    if args.serve_search_requests <= 0:
+        return first
+    m = min(args.serve_search_requests, len(n))
+    # capacity in requests / s of the first m requests at the throughput measured above
+    work_m = float(np.sum(n[:m])) * args.serve_steps
+    cap = first["throughput"] / (work_m / m)
+    service = work_m / m / first["throughput"]  # mean service time of a request alone at full throughput
+    trials = []
+    frac = 0.9
+    best = None
+    while frac >= 0.3 and len(trials) < args.serve_search_trials:
+        r = once(frac * cap, m)
+        ok = r["mean_latency_last_third_s"] <= 1.5 * r["mean_latency_first_third_s"] + service
+        r.update({"fraction_of_capacity": frac, "bounded": bool(ok)})
+        trials.append({k: r[k] for k in ("arrival_rate_hz", "fraction_of_capacity", "bounded", "p50_latency_s",
+                                         "p99_latency_s", "mean_latency_first_third_s", "mean_latency_last_third_s",
+                                         "wall_s")})
+        if ok:
+            best = r
+            break
+        frac -= 0.2
+    first["capacity_req_per_s"] = cap
+    first["sustainable_search"] = trials
+    if best is not None:
+        best["note"] = (f"highest bounded rate tried: first {m} arrivals stretched to {best['arrival_rate_hz']:.3f} / s "
+                        f"({best['fraction_of_capacity']:.0%} of the measured capacity)")
+        first["sustainable"] = best
     return first
 
 

@@ -137,6 +137,8 @@ def _declare(L):
     L.orc_source_emit.restype = C.c_int64
     L.orc_deposit_fixed.argtypes = [C.c_int, C.c_int, C.c_int64, _i32p, _i32p, _i32p, _u8p,
                                     C.c_int64, _i64p]
+    L.orc_threads.argtypes = [C.c_int]
+    L.orc_threads.restype = C.c_int
     L.orc_tally_state.argtypes = [P(OrcFields), P(OrcIon), P(OrcRun), P(OrcTallySpec), C.c_int64,
                                   _i32p, _i32p, _i32p, _dp, _dp, _dp, _dp, _dp, _u8p, _i32p, C.c_int64,
                                   P(OrcTally)]
@@ -149,6 +151,12 @@ def _ptr(a, t):
 # --------------------------------------------------------------------------
 # thin helpers
 # --------------------------------------------------------------------------
+
+def threads(n=0):
+    """Host threads of the oracle's loops over packs: set when n > 0; returns
+    the count in use."""
+    return int(lib().orc_threads(int(n)))
+
 
 def philox(ctr, key):
     ctr = (C.c_uint32 * 4)(*[int(c) & 0xFFFFFFFF for c in ctr])

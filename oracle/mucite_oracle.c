@@ -39,6 +39,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_E_CHARGE 1.602176634e-19
 #define ORC_KB 1.380649e-23
@@ -846,4 +849,17 @@ void orc_tally_state(const orc_fields *F, const orc_ion *ion, const orc_run *run
             T->loss_map[bz * ts->n_loss_r + br] += weight;
         }
     }
+}
+
+/* Host threads of the OpenMP loops over packs: n > 0 sets the count, n <= 0
+ * leaves it; returns the count the next loop uses (1 without OpenMP). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
