@@ -30,7 +30,7 @@ struct Instance {
     double rf_phase0 = 0.0;  // RF phase at the start of the current dt segment
     int64_t seg_step0 = 0;   // step at the start of the current dt segment
     double src_acc = 0.0;
-    unsigned long long *d_counters = nullptr; // [3]
+    unsigned long long *d_counters = nullptr; // [kCounters]
     // tally buffers: [0..7] count, [8..15] wsum, then hist arrays; sums in d_tsum
     unsigned long long *d_tally = nullptr;
     double *d_tsum = nullptr; // [24]: sum_ke[8], sum_teff[8], sum_sy[8]
@@ -66,6 +66,8 @@ struct mucite_ctx {
     Instance inst[MUCITE_MAX_INSTANCES];
     InstF32 *d_insts = nullptr;
     int32_t *d_tiles = nullptr;
+    unsigned *d_ticket = nullptr;   // arrival ticket of the streamed single-step kernel (zero between launches)
+    bool last_stream = false;       // the last step launch was the streamed single-step kernel
     PicInst *d_picinst = nullptr;
     DepositArgs *d_dep = nullptr;
     int32_t *d_dep_tiles = nullptr;
@@ -79,6 +81,7 @@ struct mucite_ctx {
     int use_graphs = 1;
     int64_t launches = 0;
     int64_t graph_replays = 0, graph_captures = 0;
+    InstF32 inst0{};             // host copy of the first descriptor of the last step upload
     // captured macro step of the last group (replayed while the group is unchanged)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
@@ -605,6 +608,7 @@ mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, i
     CK(cudaMemcpyAsync(ctx->d_insts, host.data(), sizeof(InstF32) * n, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                        ctx->stream));
+    ctx->inst0 = host[0]; // the descriptor a single-instance launch takes as a kernel parameter
     return MUCITE_OK;
 }
 
@@ -617,13 +621,29 @@ bool can_collide(const mucite_ctx *ctx, const Instance &I)
 
 int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int total_tiles, int chunk)
 {
+    ctx->last_stream = false;
     if (total_tiles <= 0) return 0;
     bool collide = false, extras = false;
     for (const Instance *I : grp) {
         collide = collide || can_collide(ctx, *I);
-        extras = extras || I->f32.tst || I->f32.langevin;
+        extras = extras || I->f32.tst || I->f32.langevin || I->f32.rk4;
     }
     int grid = total_tiles;
+    // one collision-free micro step of one instance: the staged streaming
+    // kernel (pool arrays 16-byte aligned for its bulk copies)
+    if (chunk == 1 && !collide && !extras && grp.size() == 1 && ctx->threads == 256) {
+        const InstF32 &P = ctx->inst0;
+        const void *arr[] = {P.xq, P.yq, P.zq, P.vx, P.vy, P.vz, P.status};
+        bool aligned = true;
+        for (const void *a : arr) aligned = aligned && ((uintptr_t)a & 15u) == 0;
+        if (aligned) {
+            const int per_sm = std::max(1, step_f32_stream_blocks_per_sm());
+            grid = std::min(total_tiles, per_sm * ctx->sm_count);
+            launch_step_f32_stream(grid_f32(ctx), P, ctx->d_insts, total_tiles, grid, ctx->d_ticket, ctx->stream);
+            ctx->last_stream = true;
+            return 1;
+        }
+    }
     // Launches of a few micro steps (streamed) default to an occupancy-sized
     // grid striding over the tiles, which spares every tile the block start
     // (descriptor copy, barriers); long fused launches and launches with
@@ -659,12 +679,16 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
     const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy;
     if (ctx->use_graphs && uniform && capturable) {
         const int chunk = P0 > 0 ? P0 : ctx->steps_per_launch;
-        const int64_t reps = (nsteps - done) / chunk;
+        // single micro steps without space charge: several per captured graph
+        // (consecutive kernels of one graph start sooner than consecutive graphs)
+        const int unroll = (P0 == 0 && chunk == 1) ? 8 : 1;
+        const int64_t reps = (nsteps - done) / ((int64_t)chunk * unroll);
         if (reps >= 2) {
             mucite_status st = ensure_rf(ctx, n * (size_t)(2 * chunk + 1));
             if (st != MUCITE_OK) return st;
             std::vector<const void *> key;
             key.push_back((const void *)(intptr_t)chunk);
+            key.push_back((const void *)(intptr_t)unroll);
             key.push_back((const void *)(intptr_t)ctx->threads);
             key.push_back((const void *)(intptr_t)ctx->persistent);
             for (Instance *I : grp) {
@@ -680,6 +704,16 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
             int tiles = 0, ptiles = 0, pmasked = 0;
             st = step_upload(ctx, grp, chunk, tiles, fused);
             if (st != MUCITE_OK) return st;
+            {
+                // a kernel may take the first descriptor by value: any change
+                // of it other than the clock needs a new capture
+                InstF32 d = ctx->inst0;
+                d.step0 = 0;
+                uint64_t h = 1469598103934665603ull; // FNV-1a
+                const unsigned char *b = reinterpret_cast<const unsigned char *>(&d);
+                for (size_t k = 0; k < sizeof d; ++k) h = (h ^ b[k]) * 1099511628211ull;
+                key.push_back((const void *)(uintptr_t)h);
+            }
             if (P0 > 0) {
                 st = pic_upload(ctx, grp, ptiles, pmasked, fused);
                 if (st != MUCITE_OK) return st;
@@ -699,9 +733,15 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 for (int attempt = 0;; ++attempt) {
                     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                     const int64_t lp = P0 > 0 ? pic_launch(ctx, (int)n, ptiles, pmasked, fused) : 0;
-                    l = lp + step_launch(ctx, grp, tiles, chunk);
-                    launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
-                    l += 1;
+                    l = lp;
+                    for (int u = 0; u < unroll; ++u) {
+                        l += step_launch(ctx, grp, tiles, chunk);
+                        // the streamed single-step kernel advances the clock itself
+                        if (!ctx->last_stream) {
+                            launch_advance_clock(ctx->d_insts, (int)n, chunk, ctx->stream);
+                            l += 1;
+                        }
+                    }
                     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
                     if (lp >= 0) {
                         if (ce != cudaSuccess)
@@ -730,8 +770,8 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
                 ctx->launches += ctx->graph_launches;
                 ctx->graph_replays += 1;
             }
-            for (Instance *I : grp) I->step += reps * chunk;
-            done += reps * chunk;
+            for (Instance *I : grp) I->step += reps * chunk * unroll;
+            done += reps * chunk * unroll;
         }
     }
     while (done < nsteps) {
@@ -802,6 +842,8 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep, sizeof(DepositArgs) * MUCITE_MAX_INSTANCES);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dep_tiles, sizeof(int32_t) * (MUCITE_MAX_INSTANCES + 1));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_limits, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_ticket, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -812,6 +854,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
         dfree(ctx->d_dep);
         dfree(ctx->d_dep_tiles);
         dfree(ctx->d_limits);
+        dfree(ctx->d_ticket);
         if (ctx->aux) cudaStreamDestroy(ctx->aux);
         delete ctx;
         return MUCITE_E_OOM;
@@ -833,6 +876,7 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_picinst);
     dfree(ctx->d_dep);
     dfree(ctx->d_dep_tiles);
+    dfree(ctx->d_ticket);
     dfree(ctx->d_rf);
     dfree(ctx->d_limits);
     drop_graph(ctx);
@@ -1042,8 +1086,8 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
     I.capacity = capacity;
     layout_of(run->precision, capacity, &I.lay);
     I.used = true;
-    CK(cudaMalloc(&I.d_counters, 3 * sizeof(unsigned long long)));
-    CK(cudaMemsetAsync(I.d_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMalloc(&I.d_counters, kCounters * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(I.d_counters, 0, kCounters * sizeof(unsigned long long), ctx->stream));
     I.tally_len = 16 + run->n_exit_bins + run->n_r_bins + run->n_ke_bins + run->n_teff_bins +
                   (int64_t)run->n_loss_r * run->n_loss_z;
     CK(cudaMalloc(&I.d_tally, I.tally_len * sizeof(unsigned long long)));
@@ -1121,7 +1165,7 @@ mucite_status mucite_resume(mucite_ctx *ctx, int instance, int64_t n_slots, int6
     drop_graph(ctx);
     I.n_slots = n_slots;
     I.step = step;
-    CK(cudaMemsetAsync(I.d_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(I.d_counters, 0, kCounters * sizeof(unsigned long long), ctx->stream));
     return MUCITE_OK;
 }
 
@@ -1240,7 +1284,7 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
         cudaGetLastError();
         return fail(ctx, MUCITE_E_OOM, "no device memory for the tuning snapshot (%zu bytes)", b);
     }
-    S.counters.resize(3 * S.sel.size());
+    S.counters.resize(kCounters * S.sel.size());
     const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
     const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
     for (size_t k = 0; k < S.sel.size(); ++k) {
@@ -1255,7 +1299,7 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
             if (I->pic.esc4)
                 CK(cudaMemcpyAsync(q + nn * 24, I->pic.esc4, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
         }
-        CK(cudaMemcpyAsync(&S.counters[3 * k], I->d_counters, 3 * sizeof(unsigned long long),
+        CK(cudaMemcpyAsync(&S.counters[kCounters * k], I->d_counters, kCounters * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1278,7 +1322,7 @@ mucite_status snapshot_restore(mucite_ctx *ctx, const Snapshot &S)
             if (I->pic.esc4)
                 CK(cudaMemcpyAsync(I->pic.esc4, q + nn * 24, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
         }
-        CK(cudaMemcpyAsync(I->d_counters, &S.counters[3 * k], 3 * sizeof(unsigned long long),
+        CK(cudaMemcpyAsync(I->d_counters, &S.counters[kCounters * k], kCounters * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, ctx->stream));
         I->step = S.step[k];
         I->n_slots = S.n_slots[k];
@@ -1447,7 +1491,7 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     CKL();
     std::vector<unsigned long long> h(I.tally_len);
     double sums[24];
-    unsigned long long cnt[3];
+    unsigned long long cnt[kCounters];
     CK(cudaMemcpyAsync(h.data(), I.d_tally, I.tally_len * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(sums, I.d_tsum, sizeof sums, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1466,6 +1510,9 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     out->collisions = (int64_t)cnt[1];
     out->candidate_overflow = (int64_t)cnt[2];
     out->step = I.step;
+    if (cnt[3] != 0)
+        return fail(ctx, MUCITE_E_TIMEOUT, "instance %d: %llu bounded device waits gave up (staged state copies "
+                    "that did not land); its state is not reliable", instance, cnt[3]);
     int64_t off = 16;
     auto copy_out = [&](int64_t *dst, int64_t len) {
         if (dst)

@@ -17,6 +17,7 @@ constexpr double kEps0 = 8.8541878128e-12; // vacuum permittivity [F/m]
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kPlanck = 6.62607015e-34;           // Planck constant [J s]
 constexpr double kR = 1.380649e-23 * 6.02214076e23;  // molar gas constant k_B N_A [J/(mol K)]
+constexpr int kCounters = 4;            // per-instance device counters (InstF32::counters)
 constexpr double kLat = 1073741824.0;      // 2^30 lattice units per R (r) or per (z1 - z0) (z)
 constexpr int kKmax = 32;                  // collision candidates examined per pack per step
 
@@ -138,7 +139,8 @@ struct InstF32 {
     float psr;                 // (pnr - 1) * 2^-30
     unsigned long long *dep_q; // charge grid the launch deposits its active packs into at the end, or NULL
     int64_t dep_qw;            // charge number * weight of a pack (its CIC contributions: dep_qw w_r w_z)
-    unsigned long long *counters; // [0] pack-steps, [1] collisions, [2] candidate-cap hits
+    unsigned long long *counters; // [0] pack-steps, [1] collisions, [2] candidate-cap hits,
+                                  // [3] bounded device waits that gave up (warps)
 };
 
 // Per-instance parameters of the plain FP64 step.

@@ -42,6 +42,16 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
                      cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
 int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras);
+// One collision-free micro step of one instance (no Eq. 7, Langevin or RK4)
+// with the pack state staged in shared memory by TMA bulk copies; the pool
+// arrays must be 16-byte aligned. Tiles of 256 packs.
+// `P` is the instance's descriptor as uploaded to d_insts[0]; the kernel
+// reads the step clock from d_insts, forms the step's RF scalar itself and
+// advances the clock by one at its end (the last block to arrive on
+// `ticket`, a device word that is zero between launches).
+void launch_step_f32_stream(const GridF32 &G, const InstF32 &P, InstF32 *d_insts, int total_tiles, int grid,
+                            unsigned *ticket, cudaStream_t s);
+int step_f32_stream_blocks_per_sm();
 void launch_step_f64(const GridF64 &G, const InstF64 &P, int64_t step, double srf, double srf_half,
                      double srf_next, cudaStream_t s);
 // Eq. 1 limits of one instance: out (device) [0] max rate, [1] max |v|,

@@ -41,6 +41,26 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
+// Dither words of pack-step (pack, n): h1 = fmix32(pack ^ key ^ n phi) with
+// phi = 2^32 / golden ratio (odd: n phi is a bijection of n, so the words of
+// one pack's steps are all distinct), h2 a bijective remix of h1 (xor-shift,
+// odd multiplier); every 10-bit field of either word is uniform. `hp` is
+// pack ^ key, formed once per pack.
+__device__ __forceinline__ uint32_t dither_word(uint32_t hp, uint32_t n)
+{
+    return fmix32(hp ^ (n * 0x9E3779B9u));
+}
+
+__device__ __forceinline__ uint32_t remix32(uint32_t h)
+{
+    return (h ^ (h >> 16)) * 0x7FEB352Du;
+}
+
+__device__ __forceinline__ uint32_t pack_key(uint32_t pack, const InstF32 &P)
+{
+    return pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1;
+}
+
 // Dither (b + 1/2) / 1024 in (0,1) from the 10 bits b of h starting at bit
 // `sh`: b becomes the top of a mantissa in [1, 2), so no integer-to-float
 // conversion is needed; dither_c is the same value minus 1/2.
@@ -485,7 +505,7 @@ __device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P
         vx[u] = P.vx[q]; vy[u] = P.vy[q]; vz[u] = P.vz[q];
         eint[u] = (kExtras && P.tst) ? P.eint[q] : 0.0f;
         lnsy[u] = (kExtras && P.tst) ? P.lnsy[q] : 0.0f;
-        hb[u] = fmix32((uint32_t)p ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
+        hb[u] = pack_key((uint32_t)p, P);
         fx[u] = (float)xq[u];
         fy[u] = (float)yq[u];
         rr[u] = lattice_r(fx[u], fy[u]);
@@ -501,7 +521,7 @@ __device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P
             gather(G, P, fx[u], fy[u], rr[u], zq[u], L);
             float kx, ky, kz;
             kick_of(P, L, s_rf[2 * k], kx, ky, kz);
-            const uint32_t h1 = fmix32(hb[u] + 2u * n), h2 = fmix32(hb[u] + 2u * n + 1u);
+            const uint32_t h1 = dither_word(hb[u], n), h2 = remix32(h1);
             float ls = lnsy[u];
             if (kExtras && P.tst) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
@@ -596,7 +616,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         if (kExtras && P.tst) lnsy = P.lnsy[p];
     }
     const uint32_t pack = (uint32_t)p;
-    const uint32_t hbase = fmix32(pack ^ (P.key0 * 0x9E3779B9u) ^ P.key1);
+    const uint32_t hbase = pack_key(pack, P);
     float fx = (float)xq, fy = (float)yq;
     float rr = lattice_r(fx, fy);
     unsigned n_coll = 0, n_ovf = 0;
@@ -623,7 +643,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
             }
         } else if (can_push) {
             const uint32_t n = (uint32_t)(P.step0 + k);
-            const uint32_t h1 = fmix32(hbase + 2u * n), h2 = fmix32(hbase + 2u * n + 1u);
+            const uint32_t h1 = dither_word(hbase, n), h2 = remix32(h1);
             if (kExtras && P.tst && !lv) {
                 // Eq. 7: d ln SY / dt = -k(T_eff), Eyring rate at the current T_eff
                 const float Te = teff_of(P, eint);
@@ -653,6 +673,98 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         }
     }
     add_counters(P, owned ? (unsigned)k : 0u, n_coll, n_ovf);
+}
+
+// RF scalar of Eq. 4 at time step0 + j/2 of an instance: the phase
+// frac(phase0 + (n - seg0) dt f) taken in FP64 from the integer step count.
+__device__ __forceinline__ float rf_scalar_at(const InstF32 &P, int64_t step0, int j)
+{
+    float v = 0.0f;
+    if (P.v_rf != 0.0 && P.dtf != 0.0) {
+        const double x = P.rf_phase0 + ((double)(step0 - P.seg_step0) + 0.5 * j) * P.dtf;
+        v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Streamed single step (one micro step per launch, collision-free, no Eq. 7,
+// Langevin or RK4; one instance). The kernel is bound by the HBM stream of
+// the pack state, 49 bytes per pack-step, and a block that loads its tile's
+// state only when it starts the tile leaves the memory system idle while it
+// computes. Here the state of the next tiles a block will take is copied to
+// shared memory by TMA bulk copies (cp.async.bulk, completion counted on an
+// mbarrier per stage) kStreamStages - 1 tiles ahead, so the HBM stream keeps
+// flowing while the block computes. The per-pack arithmetic is that of the
+// collision-free tile (same device functions), so results are identical.
+// ---------------------------------------------------------------------------
+constexpr int kStreamStages = 4;
+constexpr int kStreamTile = 256; // packs per tile: two per thread, 128 threads
+constexpr uint32_t kWaitSpins = 1u << 20;
+
+struct StreamStage {
+    int32_t xq[kStreamTile], yq[kStreamTile], zq[kStreamTile];
+    float vx[kStreamTile], vy[kStreamTile], vz[kStreamTile];
+    uint8_t status[kStreamTile];
+};
+constexpr uint32_t kStageBytes = 6 * 4 * kStreamTile + kStreamTile;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the phase of the given parity has completed; false after
+// kWaitSpins polls (a copy that never lands is reported, not waited for)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitSpins; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completion counted on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// stage the state of full tile t (kStreamTile packs from pack t * kStreamTile)
+__device__ __forceinline__ void stream_prefetch(const InstF32 &P, int64_t t, StreamStage &S, uint64_t *bar)
+{
+    const int64_t o = t * kStreamTile;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, kStageBytes);
+    bulk_g2s(S.xq, P.xq + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.yq, P.yq + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.zq, P.zq + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.vx, P.vx + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.vy, P.vy + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.vz, P.vz + o, 4 * kStreamTile, bar);
+    bulk_g2s(S.status, P.status + o, kStreamTile, bar);
 }
 
 } // namespace
@@ -703,20 +815,151 @@ __global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
     }
 }
 
+// Streamed single step over the tiles of one instance (see above). Warp 4
+// is the producer: its first lane waits until stage k has been read (the
+// "empty" barrier of the stage, one arrival per consumer warp) and refills it
+// with the state of the block's next full tile (the "full" barrier counts the
+// bytes in). Warps 0-3 consume: each waits for the stage of its tile, reads
+// its two packs per thread, releases the stage and computes, so no warp waits
+// for another. A partial last tile is read directly. The instance descriptor
+// is a kernel parameter (constant bank); only the step clock, advanced on the
+// device between graph replays, is read from the descriptor array. A wait
+// that gives up raises counters[3]; the producer then waits (bounded) for its
+// copies in flight before the block ends.
+constexpr int kStreamConsumers = 128;
+
+__global__ void __launch_bounds__(kStreamConsumers + 32, 6)
+    step_f32_stream_kernel(const __grid_constant__ GridF32 G, const __grid_constant__ InstF32 P, InstF32 *insts,
+                           int total_tiles, unsigned *ticket)
+{
+    __shared__ __align__(128) StreamStage stage[kStreamStages];
+    __shared__ __align__(8) uint64_t full_bar[kStreamStages];
+    __shared__ __align__(8) uint64_t empty_bar[kStreamStages];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < kStreamStages; ++k) {
+            mbar_init(&full_bar[k], 1);
+            mbar_init(&empty_bar[k], kStreamConsumers / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int64_t n_full = P.n_slots / kStreamTile; // tiles [0, n_full) are full
+    if (tid >= kStreamConsumers) {
+        // producer warp
+        if (tid != kStreamConsumers) return;
+        int issued[kStreamStages] = {};
+        bool failed = false;
+        for (int i = 0;; ++i) {
+            const int64_t t = blockIdx.x + (int64_t)i * gridDim.x;
+            if (t >= n_full) break;
+            const int sg = i % kStreamStages;
+            if (i >= kStreamStages && !mbar_wait(&empty_bar[sg], (uint32_t)(i / kStreamStages - 1) & 1u)) {
+                failed = true;
+                break;
+            }
+            stream_prefetch(P, t, stage[sg], &full_bar[sg]);
+            ++issued[sg];
+        }
+        // the copies of this block land before its shared memory is released
+        for (int k = 0; k < kStreamStages; ++k)
+            if (issued[k] > 0 && !mbar_wait(&full_bar[k], (uint32_t)(issued[k] - 1) & 1u)) failed = true;
+        if (failed) atomicAdd(&P.counters[3], 1ull);
+        return;
+    }
+    const int lane = tid & 31;
+    const uint32_t hk = pack_key(0u, P);
+    // the step clock (advanced on the device between graph replays) and the
+    // step's RF scalar, formed by one lane per warp (FP64) and broadcast
+    const int64_t step0 = *(volatile const int64_t *)&insts[0].step0;
+    const uint32_t n = (uint32_t)step0;
+    float srf = 0.0f;
+    if (lane == 0) srf = rf_scalar_at(P, step0, 0);
+    srf = __shfl_sync(0xffffffffu, srf, 0);
+    unsigned n_steps_done = 0;
+    bool failed = false;
+    for (int i = 0;; ++i) {
+        const int64_t t = blockIdx.x + (int64_t)i * gridDim.x;
+        if (t >= total_tiles) break;
+        const int sg = i % kStreamStages;
+        int32_t xq[2], yq[2], zq[2];
+        float vx[2], vy[2], vz[2];
+        bool own[2];
+        if (t < n_full) {
+            if (!mbar_wait(&full_bar[sg], (uint32_t)(i / kStreamStages) & 1u)) {
+                failed = true;
+                break;
+            }
+            const StreamStage &S = stage[sg];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = tid + u * kStreamConsumers;
+                own[u] = S.status[j] == MUCITE_ACTIVE;
+                xq[u] = S.xq[j]; yq[u] = S.yq[j]; zq[u] = S.zq[j];
+                vx[u] = S.vx[j]; vy[u] = S.vy[j]; vz[u] = S.vz[j];
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[sg]))
+                                        : "memory");
+        } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t p = t * kStreamTile + tid + u * kStreamConsumers;
+                const int64_t q = p < P.n_slots ? p : 0;
+                own[u] = p < P.n_slots && P.status[q] == MUCITE_ACTIVE;
+                xq[u] = P.xq[q]; yq[u] = P.yq[q]; zq[u] = P.zq[q];
+                vx[u] = P.vx[q]; vy[u] = P.vy[q]; vz[u] = P.vz[q];
+            }
+        }
+        const int64_t base = t * kStreamTile;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = tid + u * kStreamConsumers;
+            const float fx = (float)xq[u], fy = (float)yq[u];
+            Local L;
+            gather(G, P, fx, fy, lattice_r(fx, fy), zq[u], L);
+            float kx, ky, kz;
+            kick_of(P, L, srf, kx, ky, kz);
+            const uint32_t h1 = dither_word((uint32_t)(base + j) ^ hk, n), h2 = remix32(h1);
+            float gx, gy, gr;
+            const int s2 = push<false>(G, P, &srf, 0, h1, h2, kx, ky, kz, xq[u], yq[u], zq[u], vx[u], vy[u],
+                                       vz[u], gx, gy, gr);
+            if (own[u]) {
+                n_steps_done += 1u;
+                P.xq[base + j] = xq[u]; P.yq[base + j] = yq[u]; P.zq[base + j] = zq[u];
+                P.vx[base + j] = vx[u]; P.vy[base + j] = vy[u]; P.vz[base + j] = vz[u];
+                if (s2 != MUCITE_ACTIVE) {
+                    P.status[base + j] = (uint8_t)s2;
+                    P.t_term[base + j] = (int32_t)(step0 + 1);
+                } else if (P.dep_q != nullptr) {
+                    deposit_at_end(P, xq[u], yq[u], zq[u]);
+                }
+            }
+        }
+    }
+    if (failed && lane == 0) atomicAdd(&P.counters[3], 1ull);
+    // the counters of the warps that left their loop early are still added
+    add_counters(P, n_steps_done, 0u, 0u);
+    // the last block to arrive advances the instance clock by the step (every
+    // block has read it at its start) and re-arms the ticket
+    asm volatile("bar.sync 1, %0;" ::"n"(kStreamConsumers) : "memory");
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+            insts[0].step0 = step0 + 1;
+            *ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
 // RF scalars of Eq. 4 for the next `nsteps` steps of every instance at
 // half-step spacing (entry j is time step0 + j/2): the phase
 // frac(phase0 + (n - seg0) dt f) is taken in FP64 from the integer step count.
 __global__ void rf_table_kernel(const InstF32 *insts, int nsteps)
 {
     const InstF32 &P = insts[blockIdx.x];
-    for (int j = threadIdx.x; j <= 2 * nsteps; j += blockDim.x) {
-        float v = 0.0f;
-        if (P.v_rf != 0.0 && P.dtf != 0.0) {
-            const double x = P.rf_phase0 + ((double)(P.step0 - P.seg_step0) + 0.5 * j) * P.dtf;
-            v = (float)(P.v_rf * cos(2.0 * kPi * (x - floor(x)) + P.phi_rf));
-        }
-        P.rf[j] = v;
-    }
+    for (int j = threadIdx.x; j <= 2 * nsteps; j += blockDim.x) P.rf[j] = rf_scalar_at(P, P.step0, j);
 }
 
 // Instance clocks advanced on the device (graph replays).
@@ -764,6 +1007,19 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
     else
         step_f32_kernel<false, false, 6><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
                                                                                total_tiles, nsteps);
+}
+
+void launch_step_f32_stream(const GridF32 &G, const InstF32 &P, InstF32 *d_insts, int total_tiles, int grid,
+                            unsigned *ticket, cudaStream_t s)
+{
+    step_f32_stream_kernel<<<grid, kStreamConsumers + 32, 0, s>>>(G, P, d_insts, total_tiles, ticket);
+}
+
+int step_f32_stream_blocks_per_sm()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_f32_stream_kernel, kStreamConsumers + 32, 0);
+    return b;
 }
 
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)

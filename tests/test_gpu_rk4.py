@@ -80,3 +80,34 @@ def test_eq1_limits_match_oracle(mc, orc):
             else:
                 assert abs(got[k] / ref[k] - 1) < 1e-4, (k, got[k], ref[k])
         assert got[4] == 2e-9 and got[0] == pytest.approx(0.05e-6)
+
+
+def test_rk4_is_the_integrator_applied(mc, orc):
+    """The FP32 path with RK4 selected (and neither Eq. 7 nor the Langevin
+    branch) follows the oracle's RK4 and not its leapfrog: at dt = 5 ns (200
+    steps per RF period) the two integrators separate well beyond the FP32
+    tolerance."""
+    import dataclasses
+    w = _ring_vacuum(0, n=1000)
+    w.run.dt = 5e-9
+    s = orc.Sim(w)
+    s.inject()
+    st = fp32_state_from_oracle(s)
+    lf = orc.Sim(dataclasses.replace(w, run=dataclasses.replace(w.run, integrator=0)))
+    lf.inject()
+    fp32_state_from_oracle(lf)
+    ctx = mc.Context(0)
+    ctx.set_tuning(500, 128)
+    mc.load_workload(ctx, w, 0)
+    upload(ctx, 0, st)
+    ctx.step(0, 2000)
+    got = download(ctx, 0, 1000)
+    s.steps(2000)
+    lf.steps(2000)
+    act = (got["status"] == 0) & (s.status[:1000] == 0) & (lf.status[:1000] == 0)
+    assert act.mean() > 0.5
+    pos = {k: got[k][act] for k in ("x", "y", "z")}
+    e_rk4 = rel_pos_error(w.fields.grid, pos, s.x[:1000][act], s.y[:1000][act], s.z[:1000][act])
+    e_lf = rel_pos_error(w.fields.grid, pos, lf.x[:1000][act], lf.y[:1000][act], lf.z[:1000][act])
+    assert np.median(e_rk4) < 1e-5, np.median(e_rk4)
+    assert np.median(e_lf) > 10 * np.median(e_rk4), (np.median(e_lf), np.median(e_rk4))
