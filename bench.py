@@ -497,25 +497,40 @@ def parity_report(local, stream):
     out["space_charge"] = dict(workload="cylinder 1e5 packs prefilled, PIC 256x1024, one update, same state",
                                **res)
 
-    # the space-charge run as an ensemble: independent seeds, 1e5 packs (with
-    # 1e6 the beam's own field couples the packs of a run through the noise
-    # of their charge grid and even oracle-vs-oracle fails an i.i.d. KS test)
+    # the space-charge run as an ensemble: independent seeds, replicated runs
+    # (in one run every pack moves in the field of that run's own charge
+    # grid, whose noise is common to its packs: with the benchmark's 1e6
+    # packs even the oracle against itself fails an i.i.d. KS test), ten runs
+    # of 1e4 packs per side pooled
+    import numpy as np
+    nr, runs = 10_000, 10
+    pool_g, pool_o = [], []
+
     def sc(seed, prec):
-        w = W.cylinder_space_charge(n_packs=n, n_steps=0, seed=seed, precision=prec)
+        w = W.cylinder_space_charge(n_packs=nr, n_steps=0, seed=seed, precision=prec)
         w.source.current_A = 0.0
         return w
-    w = sc(2, 0)
-    _, ctx = _gpu_run(local, stream, w, None, 0)
-    for _ in range(4):
-        ctx.step(0, 100)
-    gi = _download(ctx)
-    ctx.close()
-    so = oracle.Sim(sc(1002, 1))
-    so.inject()
-    so.advance(400)
+    for r in range(runs):
+        w = sc(2 + r, 0)
+        _, ctx = _gpu_run(local, stream, w, None, 0)
+        ctx.step(0, 200)
+        pool_g.append(_download(ctx))
+        ctx.close()
+        so = oracle.Sim(sc(1002 + r, 1))
+        so.inject()
+        so.advance(200)
+        pool_o.append(so)
+
+    class _Pooled:
+        pass
+    po = _Pooled()
+    for k in ("status", "vx", "vy", "vz", "eint"):
+        setattr(po, k, np.concatenate([getattr(s_, k)[:nr] for s_ in pool_o]))
+    pg = {k: np.concatenate([g_[k][:nr] for g_ in pool_g]) for k in ("status", "vx", "vy", "vz", "eint")}
     out["space_charge_ensemble"] = {
-        "workload": "cylinder, 1e5 packs at W = 1e3, PIC 256x1024 every 10 steps, 400 micro steps, seeds 2 vs 1002",
-        "independent_seeds_fp32": _ensemble(oracle, w.ion, gi, n, so, n)}
+        "workload": "cylinder, W = 1e3, PIC 256x1024 every 10 steps, 200 micro steps; 10 runs of 1e4 packs per side "
+                    "(GPU seeds 2-11, oracle seeds 1002-1011), pooled",
+        "independent_seeds_fp32": _ensemble(oracle, w.ion, pg, nr * runs, po, nr * runs)}
     out["seconds"] = time.perf_counter() - t_start
     return out
 
@@ -1028,7 +1043,9 @@ def _paper_grid(args, local, stream, dev):
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None,
             "traffic": traffic, "kernel_ms_per_launch": launch_ms, "pack_steps_per_launch": ps / args.steps,
             "dram_bytes_per_pack_step": traffic / (ps / args.steps) if traffic else None, "profile_stale": stale,
-            "note": "DRAM bytes of the node gathers (table not L2-resident) and of the pack state, per launch"}
+            "note": "DRAM bytes of the node gathers and of the pack state per launch: the packs' neighbourhood of the "
+                    "468 MB table stays in L2 (99 % L2 hits in the ncu summary), so the launch is issue-bound like "
+                    "the ring-stack launch and this fraction is far below 1"}
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "grid": "2001x6501", "packs": args.packs,
             "micro_steps": 2000 * args.steps, "ms": ms,
             "collisions_per_pack_step": (T1["collisions"] - T0["collisions"]) / max(ps, 1), "roofline": roof}
