@@ -336,6 +336,25 @@ mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
  * Errors: MUCITE_E_ARG (persistent_blocks_per_sm outside [0, 32]). */
 mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_sm, int use_graphs);
 
+/* Contraction of the space-charge fast solve (the DST-I in z and its
+ * inverse around the per-mode tridiagonal solve; Methods, "Axisymmetric PIC
+ * space charge update"): MUCITE_DST_SIMT (default) runs both transforms as
+ * FP32 SIMT contractions that use the sine matrix's row symmetry;
+ * MUCITE_DST_TENSOR_CORES runs them on the tensor cores (tcgen05, TMA,
+ * thread-block clusters) with every operand split into a TF32 pair
+ * (x = x_hi + x_lo, products x_hi y_hi + x_hi y_lo + x_lo y_hi), which keeps
+ * the accuracy of the FP32 contraction; the FP64 refinement to 1e-6 and all
+ * other steps are the same. The choice applies to the maskless solves of the
+ * context, batched or not, so batched and single-instance runs stay
+ * bit-identical. Make it after mucite_load_fields (with a PIC grid) and
+ * before injecting instances with space charge.
+ * Errors: MUCITE_E_ARG (unknown contraction), MUCITE_E_STATE (no PIC grid
+ * loaded, instances with space charge already injected, or the tensor-core
+ * path unavailable for this device or grid). */
+#define MUCITE_DST_SIMT 0
+#define MUCITE_DST_TENSOR_CORES 1
+mucite_status mucite_set_pic_solver(mucite_ctx *ctx, int contraction);
+
 /* Number of kernels this context has launched since creation. */
 int64_t mucite_launch_count(const mucite_ctx *ctx);
 

@@ -40,6 +40,11 @@ struct Instance {
     PicInst pic{};
     InstF32 f32{};
     InstF64 f64{};
+    // tensor-core contractions of a maskless solve: transposed residual and
+    // the TMA descriptors of its operands (tc_on when all could be made)
+    bool tc_on = false;
+    float *tc_rT = nullptr, *tc_rT_lo = nullptr, *tc_hat_lo = nullptr;
+    CUtensorMap tc_maps[kTcMaps]{}; // rT, rT_lo, S, S_lo (forward), S, S_lo, hat, hat_lo (inverse)
 };
 
 } // namespace
@@ -59,6 +64,16 @@ struct mucite_ctx {
     mucite_grid pg_grid{};
     PicGeom pg{};
     float *d_S = nullptr, *d_cp = nullptr, *d_invm = nullptr, *d_lo = nullptr;
+    // tensor-core DST-I (single-instance maskless solves): the sine matrix as
+    // a TF32 pair with rows of hld floats, its TMA descriptors, and an error
+    // word raised when a bounded wait of the contraction gives up
+    float *d_Spad = nullptr, *d_Spad_lo = nullptr;
+    CUtensorMap map_S{}, map_S_lo{}, map_SA{}, map_SA_lo{}; // S as a B operand, as an A operand
+    bool tc_ok = false;              // device and PIC grid allow the tensor-core contractions
+    bool use_tc = false;             // the caller chose them (mucite_set_pic_solver)
+    int *d_tc_err = nullptr;
+    CUtensorMap *d_tc_maps = nullptr; // [MUCITE_MAX_INSTANCES][kTcMaps] descriptors of a PIC upload's plain group
+    bool tc_group = false;            // the plain solves of the last PIC upload take the tensor cores
     double *d_a = nullptr, *d_c = nullptr, *d_A = nullptr;
     uint8_t *d_pic_metal = nullptr; // metal flags of the PIC nodes
     unsigned *d_limits = nullptr;   // Eq. 1 reduction scratch [3]
@@ -200,6 +215,10 @@ void free_instance(Instance &I)
     dfree(I.pic.phi);
     dfree(I.pic.r32);
     dfree(I.pic.hat);
+    dfree(I.tc_rT);
+    dfree(I.tc_rT_lo);
+    dfree(I.tc_hat_lo);
+    I.tc_on = false;
     dfree(I.pic.d32);
     dfree(I.pic.esc);
     dfree(I.pic.er64);
@@ -223,6 +242,9 @@ void free_fields(mucite_ctx *ctx)
     dfree(ctx->d_dmask);
     for (auto &p : ctx->d_f64) dfree(p);
     dfree(ctx->d_S);
+    dfree(ctx->d_Spad);
+    dfree(ctx->d_Spad_lo);
+    ctx->tc_ok = false;
     dfree(ctx->d_cp);
     dfree(ctx->d_invm);
     dfree(ctx->d_lo);
@@ -483,6 +505,19 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in,
         if (I->pic_masked) grp.push_back(I);
     n_masked = (int)std::count_if(grp_in.begin(), grp_in.end(), [](Instance *I) { return I->pic_masked; });
     const size_t n = grp.size();
+    // the plain solves take the tensor cores when the grid's rule says so
+    // (every plain instance then has its operands)
+    const size_t n_plain = n - (size_t)n_masked;
+    bool tc = ctx->tc_ok && ctx->use_tc && n_plain > 0;
+    for (size_t k = 0; k < n_plain; ++k) tc = tc && grp[k]->tc_on;
+    ctx->tc_group = tc;
+    if (tc) {
+        std::vector<CUtensorMap> maps(n_plain * kTcMaps);
+        for (size_t k = 0; k < n_plain; ++k)
+            for (int q = 0; q < kTcMaps; ++q) maps[k * kTcMaps + q] = grp[k]->tc_maps[q];
+        CK(cudaMemcpyAsync(ctx->d_tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    }
     std::vector<DepositArgs> dep(n);
     std::vector<PicInst> pi(n);
     std::vector<int32_t> tiles(n + 1);
@@ -491,6 +526,12 @@ mucite_status pic_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp_in,
         dep[k] = deposit_args(ctx, *grp[k]);
         if (into_next) dep[k].Q = grp[k]->pic.Qn;
         pi[k] = grp[k]->pic;
+        // the transposed residual and the TF32 pairs only for solves whose
+        // contractions run on the tensor cores
+        const bool tk = tc && k < n_plain;
+        pi[k].rT = tk ? grp[k]->tc_rT : nullptr;
+        pi[k].rT_lo = tk ? grp[k]->tc_rT_lo : nullptr;
+        pi[k].hat_lo = tk ? grp[k]->tc_hat_lo : nullptr;
         tiles[k] = (int32_t)total;
         total += (grp[k]->n_slots + 255) / 256;
     }
@@ -525,7 +566,8 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked, b
     const int n_plain = n_inst - n_masked;
     if (n_plain > 0) {
         const int k = launch_pic_solve(ctx->pg, ctx->d_picinst, n_plain, kPicRefine, 1e-6, ctx->stream,
-                                       ctx->device_loops ? ctx->aux : nullptr);
+                                       ctx->device_loops ? ctx->aux : nullptr,
+                                       ctx->tc_group ? ctx->d_tc_maps : nullptr, ctx->d_tc_err);
         if (k < 0) return -1;
         l += k;
     }
@@ -844,6 +886,10 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_limits, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ticket, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_ticket, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tc_err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctx->d_tc_maps, sizeof(CUtensorMap) * kTcMaps * MUCITE_MAX_INSTANCES);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -855,6 +901,8 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
         dfree(ctx->d_dep_tiles);
         dfree(ctx->d_limits);
         dfree(ctx->d_ticket);
+        dfree(ctx->d_tc_err);
+        dfree(ctx->d_tc_maps);
         if (ctx->aux) cudaStreamDestroy(ctx->aux);
         delete ctx;
         return MUCITE_E_OOM;
@@ -877,6 +925,8 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_dep);
     dfree(ctx->d_dep_tiles);
     dfree(ctx->d_ticket);
+    dfree(ctx->d_tc_err);
+    dfree(ctx->d_tc_maps);
     dfree(ctx->d_rf);
     dfree(ctx->d_limits);
     drop_graph(ctx);
@@ -962,6 +1012,7 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
         G.dr = pic->R / (pic->nr - 1);
         G.dz = (pic->z1 - pic->z0) / (pic->nz - 1);
         G.bscale = -(kE / kLat) / (kEps0 * kPi * G.dz);
+        G.hld = (G.M + 3) / 4 * 4;
         const int M = G.M, Nu = G.Nu;
         std::vector<float> S((size_t)M * M), cp((size_t)Nu * M), invm((size_t)Nu * M), lo(Nu);
         std::vector<double> a(Nu), c(Nu), A(Nu);
@@ -1011,6 +1062,37 @@ mucite_status mucite_load_fields(mucite_ctx *ctx, const mucite_grid *g, const do
         CK(cudaMemcpy(ctx->d_a, a.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_c, c.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_A, A.data(), Nu * sizeof(double), cudaMemcpyHostToDevice));
+        // the tensor-core contractions read S through TMA: rows padded to hld
+        // floats (16-byte rows)
+        ctx->tc_ok = false;
+        if (tc_shape_ok(G) && tc_prepare()) {
+            // S = S_hi + S_lo, S_hi rounded to TF32 (10 mantissa bits, to
+            // nearest with ties away from zero: add half a unit of the 13
+            // dropped bits to the magnitude, then clear them)
+            std::vector<float> hi((size_t)M * G.hld, 0.0f), lo((size_t)M * G.hld, 0.0f);
+            for (int j = 0; j < M; ++j)
+                for (int k = 0; k < M; ++k) {
+                    const float v = S[(size_t)j * M + k];
+                    uint32_t b;
+                    std::memcpy(&b, &v, 4);
+                    b = (b + 0x1000u) & 0xFFFFE000u;
+                    float h;
+                    std::memcpy(&h, &b, 4);
+                    hi[(size_t)j * G.hld + k] = h;
+                    lo[(size_t)j * G.hld + k] = v - h;
+                }
+            CK(cudaMalloc(&ctx->d_Spad, hi.size() * sizeof(float)));
+            CK(cudaMalloc(&ctx->d_Spad_lo, lo.size() * sizeof(float)));
+            CK(cudaMemcpy(ctx->d_Spad, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(ctx->d_Spad_lo, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
+            // S is the B operand of the forward contraction and the A operand
+            // of the inverse one
+            ctx->tc_ok = make_tc_map(&ctx->map_S, ctx->d_Spad, M, M, G.hld, kTcBoxB) &&
+                         make_tc_map(&ctx->map_S_lo, ctx->d_Spad_lo, M, M, G.hld, kTcBoxB) &&
+                         make_tc_map(&ctx->map_SA, ctx->d_Spad, M, M, G.hld, kTcBoxA) &&
+                         make_tc_map(&ctx->map_SA_lo, ctx->d_Spad_lo, M, M, G.hld, kTcBoxA);
+        }
+        cudaGetLastError(); // a refused check leaves no error behind: the fast solve then stays on SIMT
         // metal flag of each PIC node: the electrode mask at the nearest static node
         std::vector<uint8_t> pm((size_t)pic->nr * pic->nz);
         const double sdr = g->R / (g->nr - 1), sdz = (g->z1 - g->z0) / (g->nz - 1);
@@ -1099,7 +1181,7 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
         CK(cudaMalloc(&I.pic.Q, nn * sizeof(unsigned long long)));
         CK(cudaMalloc(&I.pic.phi, nn * sizeof(double)));
         CK(cudaMalloc(&I.pic.r32, nu * sizeof(float)));
-        CK(cudaMalloc(&I.pic.hat, nu * sizeof(float)));
+        CK(cudaMalloc(&I.pic.hat, (size_t)G.Nu * G.hld * sizeof(float)));
         CK(cudaMalloc(&I.pic.d32, nu * sizeof(float)));
         CK(cudaMalloc(&I.pic.esc, nn * sizeof(float2)));
         CK(cudaMalloc(&I.pic.red, 8 * sizeof(double)));
@@ -1109,6 +1191,21 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
         CK(cudaMemsetAsync(I.pic.Q, 0, nn * sizeof(unsigned long long), ctx->stream));
         CK(cudaMemsetAsync(I.pic.red, 0, 8 * sizeof(double), ctx->stream));
         I.pic_masked = run->pic_masked != 0 && ctx->pic_has_metal;
+        if (ctx->tc_ok && ctx->use_tc && !I.pic_masked) {
+            const size_t nt = (size_t)G.Nu * G.hld;
+            CK(cudaMalloc(&I.tc_rT, nt * sizeof(float)));
+            CK(cudaMalloc(&I.tc_rT_lo, nt * sizeof(float)));
+            CK(cudaMalloc(&I.tc_hat_lo, nt * sizeof(float)));
+            CUtensorMap *m = I.tc_maps;
+            I.tc_on = make_tc_map(&m[0], I.tc_rT, G.Nu, G.M, G.hld, kTcBoxA) &&
+                      make_tc_map(&m[1], I.tc_rT_lo, G.Nu, G.M, G.hld, kTcBoxA) &&
+                      make_tc_map(&m[6], I.pic.hat, G.Nu, G.M, G.hld, kTcBoxB) &&
+                      make_tc_map(&m[7], I.tc_hat_lo, G.Nu, G.M, G.hld, kTcBoxB);
+            m[2] = ctx->map_S;
+            m[3] = ctx->map_S_lo;
+            m[4] = ctx->map_SA;
+            m[5] = ctx->map_SA_lo;
+        }
         if (I.pic_masked) {
             CK(cudaMalloc(&I.pic.r64, nu * sizeof(double)));
             CK(cudaMalloc(&I.pic.z64, nu * sizeof(double)));
@@ -1510,6 +1607,11 @@ mucite_status mucite_tally(mucite_ctx *ctx, int instance, mucite_tally_out *out)
     out->collisions = (int64_t)cnt[1];
     out->candidate_overflow = (int64_t)cnt[2];
     out->step = I.step;
+    int tc_err = 0;
+    CK(cudaMemcpy(&tc_err, ctx->d_tc_err, sizeof tc_err, cudaMemcpyDeviceToHost));
+    if (tc_err != 0 && I.has_pic)
+        return fail(ctx, MUCITE_E_TIMEOUT, "a bounded wait of the tensor-core DST-I gave up: the space-charge "
+                    "solution is not reliable");
     if (cnt[3] != 0)
         return fail(ctx, MUCITE_E_TIMEOUT, "instance %d: %llu bounded device waits gave up (staged state copies "
                     "that did not land); its state is not reliable", instance, cnt[3]);
@@ -1544,8 +1646,13 @@ mucite_status mucite_pic_read(mucite_ctx *ctx, int instance, int64_t *Q, double 
         CK(cudaMemcpyAsync(e.data(), I.pic.esc, nn * sizeof(float2), cudaMemcpyDeviceToHost, ctx->stream));
     }
     double red[4] = {0, 0, 0, 0};
+    int tc_err = 0;
     CK(cudaMemcpyAsync(red, I.pic.red, sizeof red, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&tc_err, ctx->d_tc_err, sizeof tc_err, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (tc_err != 0)
+        return fail(ctx, MUCITE_E_TIMEOUT, "a bounded wait of the tensor-core DST-I gave up: the space-charge "
+                    "solution is not reliable");
     for (size_t k = 0; k < e.size(); ++k) {
         if (er) er[k] = e[k].x;
         if (ez) ez[k] = e[k].y;
@@ -1648,6 +1755,21 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 }
 
 int64_t mucite_launch_count(const mucite_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+mucite_status mucite_set_pic_solver(mucite_ctx *ctx, int contraction)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (contraction != MUCITE_DST_SIMT && contraction != MUCITE_DST_TENSOR_CORES)
+        return fail(ctx, MUCITE_E_ARG, "contraction must be MUCITE_DST_SIMT or MUCITE_DST_TENSOR_CORES");
+    if (!ctx->has_pic_grid) return fail(ctx, MUCITE_E_STATE, "load fields with a PIC grid first");
+    for (auto &I : ctx->inst)
+        if (I.used && I.has_pic) return fail(ctx, MUCITE_E_STATE, "choose the solver before injecting instances");
+    if (contraction == MUCITE_DST_TENSOR_CORES && !ctx->tc_ok)
+        return fail(ctx, MUCITE_E_STATE, "the tensor-core contractions are not available for this device or grid");
+    drop_graph(ctx);
+    ctx->use_tc = contraction == MUCITE_DST_TENSOR_CORES;
+    return MUCITE_OK;
+}
 
 mucite_status mucite_graph_stats(const mucite_ctx *ctx, int64_t *replays, int64_t *captures)
 {

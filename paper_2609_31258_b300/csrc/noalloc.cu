@@ -68,7 +68,7 @@ ScratchLayout scratch_layout(int M, int Nu)
     put(L.c, (size_t)Nu * sizeof(double));
     put(L.A, (size_t)Nu * sizeof(double));
     put(L.r32, (size_t)M * Nu * sizeof(float));
-    put(L.hat, (size_t)M * Nu * sizeof(float));
+    put(L.hat, (size_t)((M + 3) / 4 * 4) * Nu * sizeof(float));
     put(L.d32, (size_t)M * Nu * sizeof(float));
     L.total = off;
     return L;
@@ -183,6 +183,7 @@ extern "C" mucite_status mucite_poisson_solve_noalloc(int device, void *cuda_str
         G.pnz = pic->nz;
         G.M = M;
         G.Nu = Nu;
+        G.hld = (M + 3) / 4 * 4;
         G.dr = pic->R / (pic->nr - 1);
         G.dz = (pic->z1 - pic->z0) / (pic->nz - 1);
         G.bscale = -(kE / kLat) / (kEps0 * kPi * G.dz);

@@ -54,6 +54,19 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return v;
 }
 
+// A solved hat value: as is, or, with the tensor-core contractions, as the
+// TF32 pair (hat rounded to TF32, hat_lo the rest).
+__device__ __forceinline__ void store_hat(const PicInst &I, size_t e, float v)
+{
+    if (I.hat_lo != nullptr) {
+        const float hi = tf32_round(v);
+        I.hat[e] = hi;
+        I.hat_lo[e] = v - hi;
+    } else {
+        I.hat[e] = v;
+    }
+}
+
 } // namespace
 
 // Cell (j * pnr + i of its lower-left node) and the four CIC contributions
@@ -219,11 +232,59 @@ __global__ void __launch_bounds__(256) residual_kernel(PicGeom G, const PicInst 
     }
 }
 
+// The residual of residual_kernel written transposed for the tensor-core
+// contractions as a TF32 pair: rT[i][j - 1] (rounded to TF32) and rT_lo (the
+// rest), i-major with leading dimension hld. A block takes
+// a 32 x 32 tile of (j, i), reads Phi and Q along i (coalesced), and writes
+// rT along j through a shared-memory transpose; ||r||^2 per block into
+// part[block] (added up in block order by check_kernel).
+__global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicInst *insts)
+{
+    __shared__ float tile[32][33];
+    __shared__ double sh[32];
+    const PicInst &I = insts[blockIdx.z];
+    if (*I.conv) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32; // q = j - 1
+    double acc = 0.0;
+    for (int r = ty; r < 32; r += 8) {
+        const int q = q0 + r, i = i0 + tx;
+        float v = 0.0f;
+        if (q < G.M && i < G.Nu) {
+            const int j = q + 1;
+            const double *ph = I.phi + (size_t)j * G.pnr + i;
+            const double c = ph[0];
+            const double w = i > 0 ? ph[-1] : 0.0;
+            const double east = ph[1];
+            const double ax = G.a[i] * w + G.c[i] * east - (G.a[i] + G.c[i]) * c +
+                              G.A[i] * (ph[G.pnr] - 2.0 * c + ph[-G.pnr]);
+            const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
+            const double res = b - ax;
+            v = (float)res;
+            acc += res * res;
+        }
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, q = q0 + tx;
+        if (i < G.Nu && q < G.M) {
+            const float v = tile[tx][r], hi = tf32_round(v);
+            I.rT[(size_t)i * G.hld + q] = hi;
+            I.rT_lo[(size_t)i * G.hld + q] = v - hi;
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) I.part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
 // Convergence decision: red[2] = ||r|| / ||b||; conv when <= tol. With
-// per-block partial sums (I.part), ||r||^2 (and, on the first check of a
-// solve, ||b||^2) are first added up over the nblk blocks in block order, so
-// the decision does not depend on the order in which the blocks finished.
-__global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double tol, int nblk, int first)
+// per-block partial sums (I.part), ||r||^2 (over the nblk blocks of the
+// residual) and, on the first check of a solve, ||b||^2 (over the nblk_b
+// blocks of bnorm_kernel) are first added up in block order, so the decision
+// does not depend on the order in which the blocks finished.
+__global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double tol, int nblk, int first,
+                                                    int nblk_b)
 {
     __shared__ double sh[32];
     const PicInst &I = insts[blockIdx.x];
@@ -236,7 +297,7 @@ __global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double
         if (first) {
             __syncthreads();
             double b = 0.0;
-            for (int k = threadIdx.x; k < nblk; k += blockDim.x) b += I.part[kRedBlocks + k];
+            for (int k = threadIdx.x; k < nblk_b; k += blockDim.x) b += I.part[kRedBlocks + k];
             b = block_sum(b, sh);
             if (threadIdx.x == 0) I.red[0] = b;
         }
@@ -328,8 +389,8 @@ __global__ void __launch_bounds__(256, 2) dst_sym_kernel(PicGeom G, const PicIns
             if (gn < No && gk < ke) {
                 if (kInv) {
                     // B(c, i) = hat[i][2c], hat[i][2c+1]
-                    y0 = R[(size_t)gn * M + 2 * gk];
-                    y1 = 2 * gk + 1 < M ? R[(size_t)gn * M + 2 * gk + 1] : 0.0f;
+                    y0 = R[(size_t)gn * G.hld + 2 * gk];
+                    y1 = 2 * gk + 1 < M ? R[(size_t)gn * G.hld + 2 * gk + 1] : 0.0f;
                 } else {
                     // B(j, c) = S[j][2c], S[j][2c+1]
                     y0 = S[(size_t)gk * M + 2 * gn];
@@ -399,7 +460,7 @@ __global__ void __launch_bounds__(256, 2) dst_sym_kernel(PicGeom G, const PicIns
             const int jm = M - 1 - gm;
             if (jm != gm) D[(size_t)jm * Nu + gn] = x0 - x1;
         } else {
-            float *D = I.hat + (size_t)gm * M;
+            float *D = I.hat + (size_t)gm * G.hld;
             D[2 * gn] = alpha * x0;
             if (2 * gn + 1 < M) D[2 * gn + 1] = alpha * x1;
         }
@@ -474,7 +535,7 @@ __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicIn
         const int i = e / kThModes, kk = e % kThModes, k = k0 + kk;
         if (k < G.M) {
             const size_t o = (size_t)i * G.M + k;
-            sh[i][kk] = I.hat[o];
+            sh[i][kk] = I.hat[(size_t)i * G.hld + k];
             sm[i][kk] = G.invm[o];
             sc[i][kk] = G.cp[o];
         }
@@ -553,7 +614,7 @@ __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicIn
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int i = e / kThModes, kk = e % kThModes, k = k0 + kk;
-        if (k < G.M) I.hat[(size_t)i * G.M + k] = sh[i][kk];
+        if (k < G.M) store_hat(I, (size_t)i * G.hld + k, sh[i][kk]);
     }
 }
 
@@ -581,7 +642,7 @@ __global__ void __launch_bounds__(256) pcr_kernel(PicGeom G, const PicInst *inst
         a = ai; // a_0 = 0: no flux through the axis
         c = i + 1 < n ? ci : 0.0f;
         b = -(ai + ci + (float)G.A[i] * lam);
-        d = I.hat[(size_t)i * G.M + k];
+        d = I.hat[(size_t)i * G.hld + k];
     }
     int cur = 0;
     sa[0][i] = a; sb[0][i] = b; sc[0][i] = c; sd[0][i] = d;
@@ -602,7 +663,7 @@ __global__ void __launch_bounds__(256) pcr_kernel(PicGeom G, const PicInst *inst
         sa[cur][i] = a; sb[cur][i] = b; sc[cur][i] = c; sd[cur][i] = d;
         __syncthreads();
     }
-    if (i < n) I.hat[(size_t)i * G.M + k] = __fdividef(d, b);
+    if (i < n) store_hat(I, (size_t)i * G.hld + k, __fdividef(d, b));
 }
 
 // Tridiagonal solve per axial mode k, in place on hat[i][k] (i = 0..Nu-1),
@@ -617,13 +678,17 @@ __global__ void __launch_bounds__(256) thomas_kernel(PicGeom G, const PicInst *i
     float y = h[0] * G.invm[k];
     h[0] = y;
     for (int i = 1; i < G.Nu; ++i) {
-        y = (h[(size_t)i * G.M] - G.lo[i] * y) * G.invm[(size_t)i * G.M + k];
-        h[(size_t)i * G.M] = y;
+        y = (h[(size_t)i * G.hld] - G.lo[i] * y) * G.invm[(size_t)i * G.M + k];
+        h[(size_t)i * G.hld] = y;
     }
     float x = y;
+    if (I.hat_lo != nullptr) store_hat(I, (size_t)(G.Nu - 1) * G.hld + k, x);
     for (int i = G.Nu - 2; i >= 0; --i) {
-        x = h[(size_t)i * G.M] - G.cp[(size_t)i * G.M + k] * x;
-        h[(size_t)i * G.M] = x;
+        x = h[(size_t)i * G.hld] - G.cp[(size_t)i * G.M + k] * x;
+        if (I.hat_lo != nullptr)
+            store_hat(I, (size_t)i * G.hld + k, x);
+        else
+            h[(size_t)i * G.hld] = x;
     }
 }
 
@@ -720,8 +785,22 @@ void launch_sym(void (*kern)(PicGeom, const PicInst *, int, float), dim3 grid, i
     cudaLaunchKernelEx(&cfg, kern, G, d_insts, splits, alpha);
 }
 
-int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s,
+                      const CUtensorMap *tc_maps, int *tc_err)
 {
+    if (tc_maps != nullptr) {
+        // hat[i][k] = 2/(M+1) sum_j rT[i][j] S[k][j]  (S symmetric)
+        launch_dst_tc(tc_maps, 0, d_insts, n_inst, true, G, (float)(2.0 / (G.M + 1)), tc_err, s);
+        if (G.Nu > 128 && G.Nu <= 256)
+            pcr_kernel<<<dim3(G.M, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        else if (G.Nu <= kThRows)
+            thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        else
+            thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        // d32[j][i] = sum_k S[j][k] hat[i][k]
+        launch_dst_tc(tc_maps, 4, d_insts, n_inst, false, G, 1.0f, tc_err, s);
+        return 3;
+    }
     // split the k range over a cluster of 2 to 8 CTAs while the 64 x 64
     // tiles would leave the SMs without a second resident CTA
     const int sms = G.n_sm > 0 ? G.n_sm : 148;
@@ -804,23 +883,34 @@ void launch_loop_ctl(const PicInst *d_insts, int n_inst, int max_passes, cudaGra
 }
 
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
-                     cudaStream_t s, cudaStream_t aux)
+                     cudaStream_t s, cudaStream_t aux, const CUtensorMap *tc_maps, int *tc_err)
 {
     int launches = 0;
     const int64_t nu = (int64_t)G.M * G.Nu;
     const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
+    // with the tensor-core contractions the residual is written transposed
+    // by 32 x 32 tiles (at most kRedBlocks, tc_shape_ok): its block partial
+    // sums are then the tiles'
+    const dim3 gt((unsigned)((G.Nu + 31) / 32), (unsigned)((G.M + 31) / 32), (unsigned)n_inst);
+    const int rblocks = tc_maps != nullptr ? (int)(gt.x * gt.y) : (int)blocks;
+    auto residual = [&](cudaStream_t st) {
+        if (tc_maps != nullptr)
+            residual_t_kernel<<<gt, 256, 0, st>>>(G, d_insts);
+        else
+            residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, st>>>(G, d_insts);
+    };
     bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
     ++launches;
     // graph capture: initial residual, then at most max_refine passes of
     // (fast solve, update, residual, check) under device control
     if (max_refine > 0 && stream_capturing(s, aux)) {
-        residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, (int)blocks, 1);
+        residual(s);
+        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, rblocks, 1, (int)blocks);
         const bool looped = capture_while(s, aux, d_insts, [&](cudaStream_t b, cudaGraphConditionalHandle h) {
-            launch_fast_solve(G, d_insts, n_inst, b);
+            launch_fast_solve(G, d_insts, n_inst, b, tc_maps, tc_err);
             update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
-            residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
-            check_kernel<<<n_inst, 256, 0, b>>>(d_insts, tol, (int)blocks, 0);
+            residual(b);
+            check_kernel<<<n_inst, 256, 0, b>>>(d_insts, tol, rblocks, 0, (int)blocks);
             launch_loop_ctl(d_insts, n_inst, max_refine, h, b);
         });
         if (!looped) return -1;
@@ -828,11 +918,11 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
         return launches + 4;
     }
     for (int it = 0; it <= max_refine; ++it) {
-        residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, (int)blocks, it == 0 ? 1 : 0);
+        residual(s);
+        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, rblocks, it == 0 ? 1 : 0, (int)blocks);
         launches += 2;
         if (it == max_refine) break;
-        launches += launch_fast_solve(G, d_insts, n_inst, s);
+        launches += launch_fast_solve(G, d_insts, n_inst, s, tc_maps, tc_err);
         update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
         launches += 1;
     }

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace mucite {
@@ -10,6 +12,7 @@ namespace mucite {
 // Fixed operator data of one PIC grid (shared by the instances using it).
 struct PicGeom {
     int pnr, pnz, M, Nu;     // M = pnz - 2 axial unknowns, Nu = pnr - 1 radial unknowns
+    int hld;                 // leading dimension of hat (M rounded up to a multiple of 4: 16-byte rows)
     double dr, dz;
     double bscale;           // -(e 2^-30) / (eps0 pi dz): node charge units -> right-hand side
     const float *S;          // [M][M] sin(pi j k / (M + 1)), j, k = 1..M
@@ -28,7 +31,11 @@ struct PicInst {
                              // step's launch, taken over by the next solve (FP32 graph replays) or NULL
     double *phi;             // [pnz][pnr] potential (zero on the Dirichlet boundary)
     float *r32;              // [M][Nu] residual in FP32
-    float *hat;              // [Nu][M] transformed residual / correction
+    float *hat;              // [Nu][hld] transformed residual / correction
+    float *hat_lo;           // [Nu][hld] with the tensor-core contractions: the tridiagonal solves write
+                             // hat rounded to TF32 into hat and the rest here; else NULL
+    float *rT, *rT_lo;       // [Nu][hld] with the tensor-core contractions: the residual written
+                             // transposed (i-major, j contiguous) as a TF32 pair; else NULL
     float *d32;              // [M][Nu] correction
     float2 *esc;             // [pnz][pnr] (E_r, E_z)
     float4 *esc4;            // [pnz-1][pnr-1][2] the same per cell, the four nodes of a cell in one
@@ -42,6 +49,16 @@ struct PicInst {
     double *part;            // [2][kRedBlocks] per-block partial sums (block-ordered reductions) or NULL
     unsigned *ticket;        // arrival counter of those partial sums (zero between launches) or NULL
 };
+
+// Tensor-core DST-I contractions (dst_tc.cu): every operand is a pair of
+// FP32 arrays, x_hi (x rounded to TF32) and x_lo = x - x_hi. Per instance
+// the TMA descriptors of a solve are kTcMaps consecutive CUtensorMap in
+// device memory: the forward contraction's A = rT (hi, lo) and B = S (hi,
+// lo), then the inverse's A = S (hi, lo) and B = hat (hi, lo).
+constexpr int kTcMaps = 8;
+// Rows of the TMA box of an A operand (output tile rows) and of a B operand
+// (output tile columns).
+constexpr int kTcBoxA = 128, kTcBoxB = 128;
 
 // Most blocks a solve kernel launches per instance (8 per SM on 148 SMs).
 constexpr int kRedBlocks = 1184;
@@ -74,9 +91,37 @@ void launch_pic_clear_next(const PicGeom &G, const PicInst *d_insts, int n_inst,
 // the solve needs instead of the fixed maximum; otherwise the passes are
 // issued as a fixed sequence whose kernels return at once after convergence.
 int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_refine, double tol,
-                     cudaStream_t s, cudaStream_t aux = nullptr);
-// Maskless fast solve A d = r: r32 -> (DST-I, Thomas per mode, inverse DST-I) -> d32.
-int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
+                     cudaStream_t s, cudaStream_t aux = nullptr, const CUtensorMap *tc_maps = nullptr,
+                     int *tc_err = nullptr);
+// Maskless fast solve A d = r: r32 -> (DST-I, Thomas per mode, inverse DST-I) -> d32;
+// with tc_maps (the instances' descriptors, kTcMaps each) the residual comes
+// as rT and both contractions run on the tensor cores.
+int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s,
+                      const CUtensorMap *tc_maps = nullptr, int *tc_err = nullptr);
+// C[m][n] = alpha sum_k A[m][k] B[n][k] per instance z (A: Mg x K, B: Ng x K,
+// K-major, each a TF32 pair of FP32 rows read by TMA through the descriptors
+// maps[z * kTcMaps + first .. + 3] = A_hi, A_lo, B_hi, B_lo), formed on the
+// tensor cores as A_hi B_hi + A_hi B_lo + A_lo B_hi; C is instance z's hat
+// (forward, leading dimension hld) or d32 (inverse, leading dimension Nu).
+// Returns false when the launch is not possible.
+bool launch_dst_tc(const CUtensorMap *maps, int first, const PicInst *d_insts, int n_inst, bool forward,
+                   const PicGeom &G, float alpha, int *err, cudaStream_t s);
+// x rounded to TF32 (10 mantissa bits, to nearest, ties away from zero).
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+// Tensor map of a row-major FP32 matrix (rows x cols, leading dimension ld
+// floats, ld * 4 a multiple of 16) for 32-column x box_rows boxes with the
+// 128-byte swizzle; false when the encoder is unavailable or refuses.
+bool make_tc_map(CUtensorMap *map, const float *base, int rows, int cols, int ld, int box_rows);
+// Whether a grid's contractions fit the tensor-core kernel.
+bool tc_shape_ok(const PicGeom &G);
+// Once per device (current) before the first tensor-core launch: sets the
+// kernel's shared-memory limit and checks that its clusters can be resident.
+bool tc_prepare();
 // Mask-aware solve by PCG preconditioned with the fast solve (pic_masked.cu).
 int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst, int max_iter, double tol,
                             cudaStream_t s, cudaStream_t aux = nullptr);

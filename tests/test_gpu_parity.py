@@ -452,3 +452,95 @@ def test_streamed_single_steps_equal_fused_launch(mc, orc, graphs):
     for k in ("count", "exit_hist", "r_hist"):
         assert (ta[k] == tb[k]).all(), k
     assert ta["pack_steps"] == tb["pack_steps"]
+
+
+# ---------------------------------------------------------------------------
+# space-charge solve with the DST-I contractions on the tensor cores
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(256, 1024), (65, 257), (150, 257)])
+def test_poisson_tensor_cores_matches_direct_solve(mc, orc, shape):
+    """tcgen05 contractions with TF32-pair operands: the same 1e-6 residual
+    (Table S2) on the oracle's operator, the potential and field of the
+    direct solve, and within a few FP32 roundings of the SIMT contractions."""
+    from oracle import poisson
+    pnr, pnz = shape
+    n = 30000
+    w = _pic_workload(n, 0, pnr, pnz)
+    s = orc.Sim(w)
+    s.inject()
+    st = fp32_state_from_oracle(s)
+    out = {}
+    for solver in (mc.DST_TENSOR_CORES, mc.DST_SIMT):
+        ctx = mc.Context(0)
+        ctx.load_fields(w.fields)
+        ctx.set_pic_solver(solver)
+        ctx.inject(0, w.ion, w.source, w.run)
+        upload(ctx, 0, st)
+        ctx.pic_update(0)
+        out[solver] = ctx.pic_read(0)
+        ctx.close()
+    got, simt = out[mc.DST_TENSOR_CORES], out[mc.DST_SIMT]
+    Q = s.deposit()
+    assert (got["Q"] == Q).all()
+    ref = poisson.solve(w.fields.pic, Q)
+    res = poisson.residual(w.fields.pic, Q, got["phi"])
+    assert got["rel_residual"] <= 1e-6 and res <= 1e-6, (got["rel_residual"], res)
+    assert got["iterations"] <= simt["iterations"] + 1
+    assert np.abs(got["phi"] - ref).max() <= 1e-4 * np.abs(ref).max()
+    er, ez = orc.efield_from_phi(ref, w.fields.pic.dr, w.fields.pic.dz)
+    scale = max(np.abs(er).max(), np.abs(ez).max())
+    assert np.abs(got["er"] - er).max() <= 1e-3 * scale
+    assert np.abs(got["ez"] - ez).max() <= 1e-3 * scale
+
+
+def test_batched_space_charge_tensor_cores_equals_alone(mc):
+    """With the tensor-core contractions, instances solved in one batch give
+    bit for bit the potentials and packs of the same instances alone."""
+    import torch
+
+    def cyl(n, seed, weight):
+        w = W.cylinder_space_charge(n_packs=n, n_steps=0, seed=seed, precision=0, pic_nr=65, pic_nz=257)
+        w.source.current_A = 0.0
+        w.source.weight = weight
+        return w
+    ws = [cyl(3000, 7, 20000), cyl(1000, 8, 5000)]
+    ctx = mc.Context(0, torch.cuda.Stream())
+    ctx.set_tuning(64, 128)
+    ctx.load_fields(ws[0].fields)
+    ctx.set_pic_solver(mc.DST_TENSOR_CORES)
+    for i, w in enumerate(ws):
+        ctx.inject(i, w.ion, w.source, w.run)
+    ctx.step(-1, 200)
+    for i, w in enumerate(ws):
+        got = download(ctx, i, w.source.n_initial)
+        pic = ctx.pic_read(i)
+        c1 = mc.Context(0)
+        c1.set_tuning(64, 128)
+        c1.load_fields(w.fields)
+        c1.set_pic_solver(mc.DST_TENSOR_CORES)
+        c1.inject(0, w.ion, w.source, w.run)
+        c1.step(0, 200)
+        ref = download(c1, 0, w.source.n_initial)
+        pref = c1.pic_read(0)
+        c1.close()
+        for k in ref:
+            assert (got[k] == ref[k]).all(), (i, k)
+        assert (pic["phi"] == pref["phi"]).all()
+    ctx.close()
+
+
+def test_pic_solver_choice_errors(mc):
+    w = _pic_workload(100, 0, 65, 257)
+    ctx = mc.Context(0)
+    with pytest.raises(mc.MuciteError) as e:
+        ctx.set_pic_solver(mc.DST_TENSOR_CORES)  # no PIC grid yet
+    assert e.value.status == mc.E_STATE
+    ctx.load_fields(w.fields)
+    with pytest.raises(mc.MuciteError) as e:
+        ctx.set_pic_solver(7)
+    assert e.value.status == mc.E_ARG
+    ctx.inject(0, w.ion, w.source, w.run)
+    with pytest.raises(mc.MuciteError) as e:
+        ctx.set_pic_solver(mc.DST_SIMT)  # instances already injected
+    assert e.value.status == mc.E_STATE
+    ctx.close()
