@@ -976,11 +976,13 @@ def _space_charge(args, local, stream, dev):
     w = W.cylinder_space_charge(n_packs=args.pic_packs, n_steps=0, precision=0)
     K = args.pic_steps
 
-    def timed(run):
+    def timed(run, solver=mucite.DST_SIMT):
         ctx = mucite.Context(local, stream)
         if args.pic_direct:
             ctx.set_launch_mode(0, False)
         ctx.load_fields(w.fields)
+        if run.pic_interval:
+            ctx.set_pic_solver(solver)
         ctx.inject(0, w.ion, w.source, run, capacity=args.pic_packs + 100_000)
         # the library's autotuner picks the launch shape (state restored after)
         tuning = None if args.no_autotune else ctx.autotune([0], 200)
@@ -1000,10 +1002,18 @@ def _space_charge(args, local, stream, dev):
 
     ms, ps, rel, tuning = timed(w.run)
     ms0, _, _, _ = timed(dataclasses.replace(w.run, pic_interval=0))
+    # the same run with the DST-I contractions on the tensor cores (TF32 pairs)
+    ms_tc, ps_tc, rel_tc, _ = timed(w.run, mucite.DST_TENSOR_CORES)
+    upd = K // w.run.pic_interval
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "packs": args.pic_packs, "micro_steps": K, "ms": ms,
-            "pic_updates": K // w.run.pic_interval, "ms_without_space_charge": ms0,
-            "ms_per_pic_update": (ms - ms0) / (K // w.run.pic_interval), "pic_share": 1.0 - ms0 / ms,
+            "pic_updates": upd, "ms_without_space_charge": ms0,
+            "ms_per_pic_update": (ms - ms0) / upd, "pic_share": 1.0 - ms0 / ms,
             "last_rel_residual": rel[0], "last_iterations": rel[1], "pic_grid": "256x1024",
+            "dst_contraction": "SIMT FP32 (default)",
+            "tensor_core_dst": {"value": ps_tc / (ms_tc * 1e-3), "ms": ms_tc, "ms_per_pic_update": (ms_tc - ms0) / upd,
+                                "pic_share": 1.0 - ms0 / ms_tc, "last_rel_residual": rel_tc[0],
+                                "last_iterations": rel_tc[1],
+                                "note": "tcgen05 kind::tf32 contractions with TF32-pair operands (mucite_set_pic_solver)"},
             "launch": "direct (fixed solve passes)" if args.pic_direct else "graph-replayed macro steps",
             "tuning": tuning}
 

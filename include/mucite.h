@@ -355,6 +355,18 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 #define MUCITE_DST_TENSOR_CORES 1
 mucite_status mucite_set_pic_solver(mucite_ctx *ctx, int contraction);
 
+/* Test hook (no counterpart in the paper; for tests of the failure path,
+ * never for production runs). MUCITE_HOOK_HOLD_STAGED_COPY with value v >= 0:
+ * the next streamed single-step launch (one collision-free micro step of one
+ * instance) withholds the staged state copies of the v-th tile of every
+ * block, so the bounded waits for them run out (about 0.25 s each); the
+ * kernel then ends without faulting, counts the waits that gave up, and
+ * mucite_tally of the instance returns MUCITE_E_TIMEOUT until mucite_resume
+ * resets its counters (the pack state of that step is not reliable). v = -1
+ * clears the hook. Errors: MUCITE_E_ARG (unknown hook or v < -1). */
+#define MUCITE_HOOK_HOLD_STAGED_COPY 1
+mucite_status mucite_test_hook(mucite_ctx *ctx, int hook, int value);
+
 /* Number of kernels this context has launched since creation. */
 int64_t mucite_launch_count(const mucite_ctx *ctx);
 

@@ -83,6 +83,7 @@ struct mucite_ctx {
     int32_t *d_tiles = nullptr;
     unsigned *d_ticket = nullptr;   // arrival ticket of the streamed single-step kernel (zero between launches)
     bool last_stream = false;       // the last step launch was the streamed single-step kernel
+    int hold_tile = -1;             // test hook: withhold the staged copies of this tile of the next streamed launch
     PicInst *d_picinst = nullptr;
     DepositArgs *d_dep = nullptr;
     int32_t *d_dep_tiles = nullptr;
@@ -329,6 +330,7 @@ void bind_params(mucite_ctx *ctx, Instance &I)
             P.psr = (float)(ctx->pg.pnr - 1) * (1.0f / 1073741824.0f);
         }
         P.counters = I.d_counters;
+        P.hold_tile = -1;
     }
     if (I.lay.pos_bytes == 8) {
         InstF64 &P = I.f64;
@@ -651,6 +653,7 @@ mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, i
     CK(cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->inst0 = host[0]; // the descriptor a single-instance launch takes as a kernel parameter
+    ctx->inst0.hold_tile = -1;
     return MUCITE_OK;
 }
 
@@ -674,7 +677,9 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
     // one collision-free micro step of one instance: the staged streaming
     // kernel (pool arrays 16-byte aligned for its bulk copies)
     if (chunk == 1 && !collide && !extras && grp.size() == 1 && ctx->threads == 256) {
-        const InstF32 &P = ctx->inst0;
+        InstF32 &P = ctx->inst0;
+        P.hold_tile = ctx->hold_tile;
+        ctx->hold_tile = -1; // one launch only
         const void *arr[] = {P.xq, P.yq, P.zq, P.vx, P.vy, P.vz, P.status};
         bool aligned = true;
         for (const void *a : arr) aligned = aligned && ((uintptr_t)a & 15u) == 0;
@@ -1755,6 +1760,15 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 }
 
 int64_t mucite_launch_count(const mucite_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+mucite_status mucite_test_hook(mucite_ctx *ctx, int hook, int value)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (hook != MUCITE_HOOK_HOLD_STAGED_COPY || value < -1)
+        return fail(ctx, MUCITE_E_ARG, "unknown test hook %d or value %d", hook, value);
+    ctx->hold_tile = value;
+    return MUCITE_OK;
+}
 
 mucite_status mucite_set_pic_solver(mucite_ctx *ctx, int contraction)
 {

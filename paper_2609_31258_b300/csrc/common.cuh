@@ -141,6 +141,8 @@ struct InstF32 {
     int64_t dep_qw;            // charge number * weight of a pack (its CIC contributions: dep_qw w_r w_z)
     unsigned long long *counters; // [0] pack-steps, [1] collisions, [2] candidate-cap hits,
                                   // [3] bounded device waits that gave up (warps)
+    int hold_tile;                // test hook of the streamed kernel: block-local tile whose staged copies
+                                  // are withheld (its waits then run out), -1 = none
 };
 
 // Per-instance parameters of the plain FP64 step.

@@ -52,7 +52,8 @@ constexpr int kChunk = 32;     // K elements per staged chunk: one 128-byte swiz
 constexpr int kSlots = 3;      // ring of staged chunks per CTA
 constexpr int kMaxChunks = 16; // chunks of one CTA's K share
 constexpr int kPadN = kTile + 4; // row stride (floats) of the partial tile in shared memory
-constexpr uint32_t kSpins = 1u << 20;
+constexpr uint32_t kSpins = 1u << 26;          // backstop on the polls of one wait
+constexpr uint64_t kWaitNs = 250ull * 1000 * 1000; // wall-clock bound of one wait (0.25 s)
 constexpr uint32_t kSlice = (uint32_t)kTile * kChunk * 4u; // bytes of one operand's chunk (16 KB)
 constexpr uint32_t kChunkBytes = 4u * kSlice;              // A_hi, A_lo, B_hi, B_lo slices of one chunk
 
@@ -67,8 +68,12 @@ __device__ __forceinline__ uint32_t su32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// true once the phase of the given parity has completed; false when it has
+// not after kWaitNs of wall-clock time (%globaltimer) or kSpins polls
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
 {
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (uint32_t it = 0; it < kSpins; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
@@ -78,6 +83,11 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
                      : "r"(bar), "r"(parity)
                      : "memory");
         if (done) return true;
+        if ((it & 63u) == 63u) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }

@@ -700,7 +700,8 @@ __device__ __forceinline__ float rf_scalar_at(const InstF32 &P, int64_t step0, i
 // ---------------------------------------------------------------------------
 constexpr int kStreamStages = 4;
 constexpr int kStreamTile = 256; // packs per tile: two per thread, 128 threads
-constexpr uint32_t kWaitSpins = 1u << 20;
+constexpr uint32_t kWaitSpins = 1u << 26;          // backstop on the polls of one wait
+constexpr uint64_t kWaitNs = 250ull * 1000 * 1000; // wall-clock bound of one wait (0.25 s)
 
 struct StreamStage {
     int32_t xq[kStreamTile], yq[kStreamTile], zq[kStreamTile];
@@ -725,11 +726,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-// true once the phase of the given parity has completed; false after
-// kWaitSpins polls (a copy that never lands is reported, not waited for)
+// true once the phase of the given parity has completed; false when it has
+// not after kWaitNs of wall-clock time (%globaltimer) or kWaitSpins polls: a
+// copy that never lands is reported, not waited for
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = smem_u32(bar);
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (uint32_t it = 0; it < kWaitSpins; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
@@ -739,6 +743,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
                      : "r"(a), "r"(parity)
                      : "memory");
         if (done) return true;
+        if ((it & 63u) == 63u) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }
@@ -858,6 +867,7 @@ __global__ void __launch_bounds__(kStreamConsumers + 32, 6)
                 failed = true;
                 break;
             }
+            if (i == P.hold_tile) continue; // test hook: this tile's copies are withheld
             stream_prefetch(P, t, stage[sg], &full_bar[sg]);
             ++issued[sg];
         }

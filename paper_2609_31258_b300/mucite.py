@@ -25,7 +25,8 @@ EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_
            "mucite_step_set", "mucite_autotune",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
-           "mucite_dt_limits", "mucite_graph_stats", "mucite_set_pic_solver"]
+           "mucite_dt_limits", "mucite_graph_stats", "mucite_set_pic_solver", "mucite_test_hook"]
+HOOK_HOLD_STAGED_COPY = 1
 DST_SIMT, DST_TENSOR_CORES = 0, 1
 
 
@@ -125,6 +126,7 @@ def lib():
         L.mucite_sync.argtypes = [vp]
         L.mucite_graph_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.mucite_set_pic_solver.argtypes = [vp, C.c_int]
+        L.mucite_test_hook.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_poisson_solve_noalloc.argtypes = [C.c_int, vp, C.POINTER(Grid), vp, vp, vp, vp]
         L.mucite_set_dt.argtypes = [vp, C.c_int, C.c_double]
         L.mucite_dt_limits.argtypes = [vp, C.c_int, dp]
@@ -314,6 +316,10 @@ class Context:
         """DST_SIMT (default) or DST_TENSOR_CORES for the space-charge solve's
         contractions; after load_fields, before injecting instances."""
         self._check(lib().mucite_set_pic_solver(self._p, int(contraction)))
+
+    def test_hook(self, hook, value):
+        """Failure-path test hook (see include/mucite.h); not for production runs."""
+        self._check(lib().mucite_test_hook(self._p, int(hook), int(value)))
 
     def graph_stats(self):
         """(macro-step graphs replayed, graphs captured) since creation."""
