@@ -736,20 +736,24 @@ def main():
     fp64 = None
     if not args.no_fp64:
         fp64 = _fp64(args, w, local, stream, dev)
+    # the single-GPU sections (streamed push, sweep, space charge, paper grid,
+    # serving) describe one device: they run at N = 1 only, so a multi-rank
+    # run times the replicated step and stays short
+    one = ws == 1
     streamed = None
-    if not args.no_streamed:
+    if one and not args.no_streamed:
         streamed = _streamed_push(args, local, stream, dev, peaks)
     sweep = None
-    if not args.no_sweep:
+    if one and not args.no_sweep:
         sweep = _sweep(args, local, stream, dev)
     space_charge = None
-    if not args.no_pic:
+    if one and not args.no_pic:
         space_charge = _space_charge(args, local, stream, dev)
     paper = None
-    if not args.no_paper_grid:
+    if one and not args.no_paper_grid:
         paper = _paper_grid(args, local, stream, dev)
     serve = None
-    if not args.no_serving:
+    if one and not args.no_serving:
         serve = _serving(args, local)
 
     # CPU-baseline leg (rank 0): the oracle timed on the host cores, its rows
@@ -758,9 +762,10 @@ def main():
     cpu = parity = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_run()
-        cpu["rows"] = cpu_baseline_rows()
-        if not args.no_parity:
-            parity = parity_report(local, stream)
+        if one:
+            cpu["rows"] = cpu_baseline_rows()
+            if not args.no_parity:
+                parity = parity_report(local, stream)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
