@@ -583,8 +583,7 @@ int64_t pic_launch(mucite_ctx *ctx, int n_inst, int total_tiles, int n_masked, b
         launch_esc(Gm, ctx->d_picinst + n_plain, n_masked, ctx->stream);
         l += k + 1;
     }
-    launch_esc_cells(ctx->pg, ctx->d_picinst, n_inst, ctx->stream);
-    return l + 1;
+    return l;
 }
 
 mucite_status pic_update_group(mucite_ctx *ctx, const std::vector<Instance *> &grp)
@@ -668,10 +667,11 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
 {
     ctx->last_stream = false;
     if (total_tiles <= 0) return 0;
-    bool collide = false, extras = false;
+    bool collide = false, extras = false, pic = false;
     for (const Instance *I : grp) {
         collide = collide || can_collide(ctx, *I);
         extras = extras || I->f32.tst || I->f32.langevin || I->f32.rk4;
+        pic = pic || I->has_pic;
     }
     int grid = total_tiles;
     // one collision-free micro step of one instance: the staged streaming
@@ -699,11 +699,11 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
     // different times: 4.5 % less time per step in 10-step launches).
     const int pers = ctx->persistent > 0 ? ctx->persistent : (chunk <= 16 && !collide ? 32 : 0);
     if (pers > 0) {
-        const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(grid_f32(ctx), ctx->threads, chunk, collide, extras)));
+        const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(grid_f32(ctx), ctx->threads, chunk, collide, extras, pic)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
     }
     launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,
-                    chunk, grid, collide, extras, ctx->stream);
+                    chunk, grid, collide, extras, pic, ctx->stream);
     return 2;
 }
 
@@ -1217,10 +1217,10 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
             CK(cudaMalloc(&I.pic.q64, nu * sizeof(double)));
             CK(cudaMalloc(&I.pic.p64, nn * sizeof(double)));
             CK(cudaMemsetAsync(I.pic.p64, 0, nn * sizeof(double), ctx->stream));
-            CK(cudaMalloc(&I.pic.ticket, sizeof(unsigned)));
-            CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         }
         CK(cudaMalloc(&I.pic.part, 2 * kRedBlocks * sizeof(double)));
+        CK(cudaMalloc(&I.pic.ticket, sizeof(unsigned)));
+        CK(cudaMemsetAsync(I.pic.ticket, 0, sizeof(unsigned), ctx->stream));
         if (run->precision == MUCITE_FP32) {
             const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
             CK(cudaMalloc(&I.pic.Qn, nn * sizeof(unsigned long long)));

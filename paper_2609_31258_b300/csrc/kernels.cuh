@@ -37,11 +37,14 @@ struct TallyArgs {
 void launch_inject(const InjectArgs &A, cudaStream_t s);
 void launch_tally(const TallyArgs &A, cudaStream_t s);
 // grid == total_tiles: one tile per block; a smaller grid strides over the tiles.
+// esc_cache: the collision tiles keep each lane's last PIC cell in shared
+// memory (for groups with space charge).
 void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
                      int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
-                     cudaStream_t s);
+                     bool esc_cache, cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
-int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras);
+int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras,
+                           bool esc_cache);
 // One collision-free micro step of one instance (no Eq. 7, Langevin or RK4)
 // with the pack state staged in shared memory by TMA bulk copies; the pool
 // arrays must be 16-byte aligned. Tiles of 256 packs.

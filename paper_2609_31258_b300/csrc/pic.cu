@@ -54,6 +54,71 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return v;
 }
 
+// Row-blocked loops of the grid kernels: a block of 256 threads covers
+// 256 >> lw rows of width 2^lw (the smallest power of two >= the row length
+// n, from 32 to 256; longer rows are walked in steps of 256), so a thread's
+// node follows from shifts and masks instead of an index division.
+__host__ __device__ __forceinline__ int row_shift(int n)
+{
+    int lw = 5;
+    while ((1 << lw) < n && lw < 8) ++lw;
+    return lw;
+}
+
+// Blocks of a row-blocked launch over `rows` rows of length n.
+inline unsigned row_blocks(int rows, int n)
+{
+    const int per = 256 >> row_shift(n);
+    return (unsigned)std::min((rows + per - 1) / per, kRedBlocks);
+}
+
+// End of a residual launch for one instance, called by all threads of each
+// of its nblk blocks (this one is block blk) with the thread's partial sums
+// of ||r||^2 and, on the first residual of a solve, ||b||^2: every block
+// stores its partials, and the last block to arrive adds them up in block
+// order and takes the convergence decision -- red[2] = ||r|| / ||b||, conv
+// when <= tol, else one more correction pass counted in red[3]. The sums and
+// the decision do not depend on the order in which the blocks finished.
+template <bool kFirst>
+__device__ void residual_close(const PicInst &I, double rr, double bb, double tol, unsigned blk, unsigned nblk,
+                               double *sh)
+{
+    __shared__ bool last;
+    rr = block_sum(rr, sh);
+    if (kFirst) {
+        __syncthreads();
+        bb = block_sum(bb, sh);
+    }
+    if (threadIdx.x == 0) {
+        I.part[blk] = rr;
+        if (kFirst) I.part[kRedBlocks + blk] = bb;
+        __threadfence();
+        last = atomicAdd(I.ticket, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (unsigned k = threadIdx.x; k < nblk; k += blockDim.x) {
+        a += __ldcg(I.part + k);
+        if (kFirst) b += __ldcg(I.part + kRedBlocks + k);
+    }
+    a = block_sum(a, sh);
+    if (kFirst) {
+        __syncthreads();
+        b = block_sum(b, sh);
+    }
+    if (threadIdx.x != 0) return;
+    I.red[1] = a;
+    if (kFirst) I.red[0] = b;
+    const double bn = kFirst ? b : I.red[0];
+    const double rel = bn > 0.0 ? sqrt(a / bn) : 0.0;
+    I.red[2] = rel;
+    if (rel <= tol) *I.conv = 1;
+    else I.red[3] += 1.0;
+    *I.ticket = 0u;
+}
+
 // A solved hat value: as is, or, with the tensor-core contractions, as the
 // TF32 pair (hat rounded to TF32, hat_lo the rest).
 __device__ __forceinline__ void store_hat(const PicInst &I, size_t e, float v)
@@ -183,62 +248,44 @@ __global__ void __launch_bounds__(256) pic_clear_next_kernel(PicGeom G, const Pi
         I.Qn[e] = 0ull;
 }
 
-// ||b||^2 over the unknowns; also clears the convergence flag and counters.
-__global__ void __launch_bounds__(256) bnorm_kernel(PicGeom G, const PicInst *insts)
-{
-    __shared__ double sh[32];
-    const PicInst &I = insts[blockIdx.z];
-    const int64_t n = (int64_t)G.M * G.Nu;
-    double acc = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
-        const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
-        acc += b * b;
-    }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        if (I.part) I.part[kRedBlocks + blockIdx.x] = acc; // added up in block order by check_kernel
-        else atomicAdd(&I.red[0], acc);
-    }
-}
-
-// r = b - A Phi (FP64) on the unknowns; r32 = (float) r; ||r||^2 into red[1].
-__global__ void __launch_bounds__(256) residual_kernel(PicGeom G, const PicInst *insts)
+// r = b - A Phi (FP64) on the unknowns, r32 = (float) r; ||r||^2 (and, on
+// the first residual of a solve, ||b||^2) and the convergence decision by
+// residual_close. Rows q = j - 1 of the unknowns, row-blocked.
+template <bool kFirst>
+__global__ void __launch_bounds__(256) residual_kernel(PicGeom G, const PicInst *insts, double tol)
 {
     __shared__ double sh[32];
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
-    const int64_t n = (int64_t)G.M * G.Nu;
-    double acc = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
-        const double *ph = I.phi + (size_t)j * G.pnr + i;
-        const double c = ph[0];
-        const double w = i > 0 ? ph[-1] : 0.0;
-        const double east = ph[1]; // i + 1 <= pnr - 1, Phi = 0 there
-        const double ax = G.a[i] * w + G.c[i] * east - (G.a[i] + G.c[i]) * c +
-                          G.A[i] * (ph[G.pnr] - 2.0 * c + ph[-G.pnr]);
-        const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
-        const double r = b - ax;
-        I.r32[e] = (float)r;
-        acc += r * r;
+    const int lw = row_shift(G.Nu), per = 256 >> lw;
+    const int sub = threadIdx.x >> lw, t = threadIdx.x & ((1 << lw) - 1);
+    double rr = 0.0, bb = 0.0;
+    for (int q = blockIdx.x * per + sub; q < G.M; q += gridDim.x * per) {
+        const int j = q + 1;
+        for (int i = t; i < G.Nu; i += 1 << lw) {
+            const double *ph = I.phi + (size_t)j * G.pnr + i;
+            const double c = ph[0];
+            const double w = i > 0 ? ph[-1] : 0.0;
+            const double east = ph[1]; // i + 1 <= pnr - 1, Phi = 0 there
+            const double ax = G.a[i] * w + G.c[i] * east - (G.a[i] + G.c[i]) * c +
+                              G.A[i] * (ph[G.pnr] - 2.0 * c + ph[-G.pnr]);
+            const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
+            const double r = b - ax;
+            I.r32[(size_t)q * G.Nu + i] = (float)r;
+            rr += r * r;
+            if (kFirst) bb += b * b;
+        }
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        if (I.part) I.part[blockIdx.x] = acc; // added up in block order by check_kernel
-        else atomicAdd(&I.red[1], acc);
-    }
+    residual_close<kFirst>(I, rr, bb, tol, blockIdx.x, gridDim.x, sh);
 }
 
 // The residual of residual_kernel written transposed for the tensor-core
 // contractions as a TF32 pair: rT[i][j - 1] (rounded to TF32) and rT_lo (the
-// rest), i-major with leading dimension hld. A block takes
-// a 32 x 32 tile of (j, i), reads Phi and Q along i (coalesced), and writes
-// rT along j through a shared-memory transpose; ||r||^2 per block into
-// part[block] (added up in block order by check_kernel).
-__global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicInst *insts)
+// rest), i-major with leading dimension hld. A block takes a 32 x 32 tile of
+// (j, i), reads Phi and Q along i (coalesced), and writes rT along j through
+// a shared-memory transpose; the norms and the decision as residual_kernel.
+template <bool kFirst>
+__global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicInst *insts, double tol)
 {
     __shared__ float tile[32][33];
     __shared__ double sh[32];
@@ -246,7 +293,7 @@ __global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicIns
     if (*I.conv) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32; // q = j - 1
-    double acc = 0.0;
+    double rr = 0.0, bb = 0.0;
     for (int r = ty; r < 32; r += 8) {
         const int q = q0 + r, i = i0 + tx;
         float v = 0.0f;
@@ -261,7 +308,8 @@ __global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicIns
             const double b = G.bscale * (double)(long long)I.Q[(size_t)j * G.pnr + i];
             const double res = b - ax;
             v = (float)res;
-            acc += res * res;
+            rr += res * res;
+            if (kFirst) bb += b * b;
         }
         tile[r][tx] = v;
     }
@@ -274,41 +322,7 @@ __global__ void __launch_bounds__(256) residual_t_kernel(PicGeom G, const PicIns
             I.rT_lo[(size_t)i * G.hld + q] = v - hi;
         }
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) I.part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
-}
-
-// Convergence decision: red[2] = ||r|| / ||b||; conv when <= tol. With
-// per-block partial sums (I.part), ||r||^2 (over the nblk blocks of the
-// residual) and, on the first check of a solve, ||b||^2 (over the nblk_b
-// blocks of bnorm_kernel) are first added up in block order, so the decision
-// does not depend on the order in which the blocks finished.
-__global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double tol, int nblk, int first,
-                                                    int nblk_b)
-{
-    __shared__ double sh[32];
-    const PicInst &I = insts[blockIdx.x];
-    if (*I.conv) return;
-    if (I.part) {
-        double a = 0.0;
-        for (int k = threadIdx.x; k < nblk; k += blockDim.x) a += I.part[k];
-        a = block_sum(a, sh);
-        if (threadIdx.x == 0) I.red[1] = a;
-        if (first) {
-            __syncthreads();
-            double b = 0.0;
-            for (int k = threadIdx.x; k < nblk_b; k += blockDim.x) b += I.part[kRedBlocks + k];
-            b = block_sum(b, sh);
-            if (threadIdx.x == 0) I.red[0] = b;
-        }
-    }
-    if (threadIdx.x != 0) return;
-    const double bb = I.red[0], rr = I.red[1];
-    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-    I.red[2] = rel;
-    I.red[1] = 0.0;
-    if (rel <= tol) *I.conv = 1;
-    else I.red[3] += 1.0;
+    residual_close<kFirst>(I, rr, bb, tol, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, sh);
 }
 
 // DST-I contractions of the fast solve with the sine matrix's symmetry:
@@ -331,8 +345,10 @@ __global__ void __launch_bounds__(256) check_kernel(const PicInst *insts, double
 // CTA leaves its partial tiles in its shared memory and, after a cluster
 // barrier, CTA r adds the partials of its share of the rows through
 // distributed shared memory in rank order. Every output's sum has a fixed
-// order, so results are deterministic.
-template <bool kInv>
+// order, so results are deterministic. With kAcc (inverse only) the
+// correction is not stored but added to Phi at once, Phi[j+1][i] +=
+// (double) d[j][i], the refinement's update fused into the epilogue.
+template <bool kInv, bool kAcc = false>
 __global__ void __launch_bounds__(256, 2) dst_sym_kernel(PicGeom G, const PicInst *insts, int splits, float alpha)
 {
     constexpr int KS = 16, BM = 64, BN = 64, PAD = 4;
@@ -454,7 +470,11 @@ __global__ void __launch_bounds__(256, 2) dst_sym_kernel(PicGeom G, const PicIns
     auto put = [&](int mm, int nn, float x0, float x1) {
         const int gm = m0 + mm, gn = n0 + nn;
         if (gm >= Mo || gn >= No) return;
-        if (kInv) {
+        if (kInv && kAcc) {
+            I.phi[(size_t)(gm + 1) * G.pnr + gn] += (double)(x0 + x1);
+            const int jm = M - 1 - gm;
+            if (jm != gm) I.phi[(size_t)(jm + 1) * G.pnr + gn] += (double)(x0 - x1);
+        } else if (kInv) {
             float *D = I.d32;
             D[(size_t)gm * Nu + gn] = x0 + x1;
             const int jm = M - 1 - gm;
@@ -692,18 +712,23 @@ __global__ void __launch_bounds__(256) thomas_kernel(PicGeom G, const PicInst *i
     }
 }
 
+// Phi += (double) d32 on the unknowns (row-blocked like residual_kernel).
 __global__ void __launch_bounds__(256) update_kernel(PicGeom G, const PicInst *insts)
 {
     const PicInst &I = insts[blockIdx.z];
     if (*I.conv) return;
-    const int64_t n = (int64_t)G.M * G.Nu;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / G.Nu) + 1, i = (int)(e % G.Nu);
-        I.phi[(size_t)j * G.pnr + i] += (double)I.d32[e];
-    }
+    const int lw = row_shift(G.Nu), per = 256 >> lw;
+    const int sub = threadIdx.x >> lw, t = threadIdx.x & ((1 << lw) - 1);
+    for (int q = blockIdx.x * per + sub; q < G.M; q += gridDim.x * per)
+        for (int i = t; i < G.Nu; i += 1 << lw)
+            I.phi[(size_t)(q + 1) * G.pnr + i] += (double)I.d32[(size_t)q * G.Nu + i];
 }
 
+// E_SCE at the nodes (esc, and er64 / ez64 for FP64 instances) and, for
+// the instances that have esc4, regrouped per cell in the same pass: node
+// (i, j) is corner 00 of cell (i, j), 10 of cell (i-1, j), 01 of cell
+// (i, j-1) and 11 of cell (i-1, j-1), the float2 slots 0..3 of a cell's
+// 32 bytes. Rows j of the grid, row-blocked.
 __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *insts)
 {
     // FP64 division is slow on this part: the four step reciprocals are
@@ -718,24 +743,38 @@ __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *inst
     __syncthreads();
     const double idr = rcp[0], i2dr = rcp[1], idz = rcp[2], i2dz = rcp[3];
     const PicInst &I = insts[blockIdx.z];
-    const int64_t n = (int64_t)G.pnr * G.pnz;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % G.pnr), j = (int)(e / G.pnr);
-        const double *ph = I.phi + e;
-        double dpr, dpz;
-        if (i == 0) dpr = 0.0;
-        else if (i == G.pnr - 1) dpr = (ph[0] - ph[-1]) * idr;
-        else dpr = (ph[1] - ph[-1]) * i2dr;
-        if (j == 0) dpz = (ph[G.pnr] - ph[0]) * idz;
-        else if (j == G.pnz - 1) dpz = (ph[0] - ph[-G.pnr]) * idz;
-        else dpz = (ph[G.pnr] - ph[-G.pnr]) * i2dz;
-        I.esc[e] = make_float2((float)-dpr, (float)-dpz);
-        if (I.er64) {
-            I.er64[e] = -dpr;
-            I.ez64[e] = -dpz;
+    const int lw = row_shift(G.pnr), per = 256 >> lw;
+    const int sub = threadIdx.x >> lw, t = threadIdx.x & ((1 << lw) - 1);
+    const int cr = G.pnr - 1, cz = G.pnz - 1;
+    float2 *c4 = reinterpret_cast<float2 *>(I.esc4);
+    for (int j = blockIdx.x * per + sub; j < G.pnz; j += gridDim.x * per)
+        for (int i = t; i < G.pnr; i += 1 << lw) {
+            const size_t e = (size_t)j * G.pnr + i;
+            const double *ph = I.phi + e;
+            double dpr, dpz;
+            if (i == 0) dpr = 0.0;
+            else if (i == G.pnr - 1) dpr = (ph[0] - ph[-1]) * idr;
+            else dpr = (ph[1] - ph[-1]) * i2dr;
+            if (j == 0) dpz = (ph[G.pnr] - ph[0]) * idz;
+            else if (j == G.pnz - 1) dpz = (ph[0] - ph[-G.pnr]) * idz;
+            else dpz = (ph[G.pnr] - ph[-G.pnr]) * i2dz;
+            const float2 v = make_float2((float)-dpr, (float)-dpz);
+            I.esc[e] = v;
+            if (I.er64) {
+                I.er64[e] = -dpr;
+                I.ez64[e] = -dpz;
+            }
+            if (c4 != nullptr) {
+                if (j < cz) {
+                    if (i < cr) c4[4 * ((size_t)j * cr + i)] = v;
+                    if (i > 0) c4[4 * ((size_t)j * cr + i - 1) + 1] = v;
+                }
+                if (j > 0) {
+                    if (i < cr) c4[4 * ((size_t)(j - 1) * cr + i) + 2] = v;
+                    if (i > 0) c4[4 * ((size_t)(j - 1) * cr + i - 1) + 3] = v;
+                }
+            }
         }
-    }
 }
 
 void launch_pic_prepare(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
@@ -786,7 +825,7 @@ void launch_sym(void (*kern)(PicGeom, const PicInst *, int, float), dim3 grid, i
 }
 
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s,
-                      const CUtensorMap *tc_maps, int *tc_err)
+                      const CUtensorMap *tc_maps, int *tc_err, bool acc_phi)
 {
     if (tc_maps != nullptr) {
         // hat[i][k] = 2/(M+1) sum_j rT[i][j] S[k][j]  (S symmetric)
@@ -799,7 +838,9 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
             thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
         // d32[j][i] = sum_k S[j][k] hat[i][k]
         launch_dst_tc(tc_maps, 4, d_insts, n_inst, false, G, 1.0f, tc_err, s);
-        return 3;
+        if (!acc_phi) return 3;
+        update_kernel<<<dim3(row_blocks(G.M, G.Nu), 1, n_inst), 256, 0, s>>>(G, d_insts);
+        return 4;
     }
     // split the k range over a cluster of 2 to 8 CTAs while the 64 x 64
     // tiles would leave the SMs without a second resident CTA
@@ -822,38 +863,15 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
         thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
     else
         thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    // d32[j][i] = sum_k S[j][k] hat[i][k]
-    launch_sym(dst_sym_kernel<true>, gi, splits, G, d_insts, 1.0f, s);
+    // d32[j][i] = sum_k S[j][k] hat[i][k], or Phi[j+1][i] += that
+    launch_sym(acc_phi ? dst_sym_kernel<true, true> : dst_sym_kernel<true, false>, gi, splits, G, d_insts, 1.0f,
+               s);
     return 3;
-}
-
-__global__ void __launch_bounds__(256) esc_cells_kernel(PicGeom G, const PicInst *insts)
-{
-    const PicInst &I = insts[blockIdx.z];
-    if (I.esc4 == nullptr) return;
-    const int cr = G.pnr - 1;
-    const int64_t n = (int64_t)cr * (G.pnz - 1);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % cr), j = (int)(e / cr);
-        const float2 *s = I.esc + (size_t)j * G.pnr + i;
-        const float2 e00 = s[0], e10 = s[1], e01 = s[G.pnr], e11 = s[G.pnr + 1];
-        I.esc4[2 * e] = make_float4(e00.x, e00.y, e10.x, e10.y);
-        I.esc4[2 * e + 1] = make_float4(e01.x, e01.y, e11.x, e11.y);
-    }
-}
-
-void launch_esc_cells(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
-{
-    const int64_t nc = (int64_t)(G.pnr - 1) * (G.pnz - 1);
-    esc_cells_kernel<<<dim3((unsigned)std::min<int64_t>((nc + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(
-        G, d_insts);
 }
 
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
 {
-    const int64_t nn = (int64_t)G.pnr * G.pnz;
-    esc_kernel<<<dim3((unsigned)std::min<int64_t>((nn + 255) / 256, 1184), 1, n_inst), 256, 0, s>>>(G, d_insts);
+    esc_kernel<<<dim3(row_blocks(G.pnz, G.pnr), 1, n_inst), 256, 0, s>>>(G, d_insts);
 }
 
 __global__ void loop_reset_kernel(const PicInst *insts)
@@ -871,6 +889,22 @@ __global__ void loop_ctl_kernel(const PicInst *insts, int n_inst, int max_passes
     cudaGraphSetConditional(h, (open && c < (double)max_passes) ? 1u : 0u);
 }
 
+__global__ void loop_open_kernel(const PicInst *insts, int n_inst, int done, int max_passes,
+                                 cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    insts[0].red[7] = (double)done;
+    bool open = false;
+    for (int i = 0; i < n_inst; ++i) open = open || *insts[i].conv == 0;
+    cudaGraphSetConditional(h, (open && done < max_passes) ? 1u : 0u);
+}
+
+void launch_loop_open(const PicInst *d_insts, int n_inst, int done, int max_passes, cudaGraphConditionalHandle h,
+                      cudaStream_t s)
+{
+    loop_open_kernel<<<1, 32, 0, s>>>(d_insts, n_inst, done, max_passes, h);
+}
+
 void launch_loop_reset(const PicInst *d_insts, cudaStream_t s)
 {
     loop_reset_kernel<<<1, 32, 0, s>>>(d_insts);
@@ -886,45 +920,54 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
                      cudaStream_t s, cudaStream_t aux, const CUtensorMap *tc_maps, int *tc_err)
 {
     int launches = 0;
-    const int64_t nu = (int64_t)G.M * G.Nu;
-    const unsigned blocks = (unsigned)std::min<int64_t>((nu + 255) / 256, 1184);
     // with the tensor-core contractions the residual is written transposed
-    // by 32 x 32 tiles (at most kRedBlocks, tc_shape_ok): its block partial
-    // sums are then the tiles'
+    // by 32 x 32 tiles (at most kRedBlocks, tc_shape_ok)
     const dim3 gt((unsigned)((G.Nu + 31) / 32), (unsigned)((G.M + 31) / 32), (unsigned)n_inst);
-    const int rblocks = tc_maps != nullptr ? (int)(gt.x * gt.y) : (int)blocks;
-    auto residual = [&](cudaStream_t st) {
-        if (tc_maps != nullptr)
-            residual_t_kernel<<<gt, 256, 0, st>>>(G, d_insts);
-        else
-            residual_kernel<<<dim3(blocks, 1, n_inst), 256, 0, st>>>(G, d_insts);
+    const dim3 gr(row_blocks(G.M, G.Nu), 1, (unsigned)n_inst);
+    // each residual also takes the convergence decision (residual_close);
+    // the first of a solve also forms ||b||^2
+    auto residual = [&](cudaStream_t st, bool first) {
+        if (tc_maps != nullptr) {
+            if (first) residual_t_kernel<true><<<gt, 256, 0, st>>>(G, d_insts, tol);
+            else residual_t_kernel<false><<<gt, 256, 0, st>>>(G, d_insts, tol);
+        } else {
+            if (first) residual_kernel<true><<<gr, 256, 0, st>>>(G, d_insts, tol);
+            else residual_kernel<false><<<gr, 256, 0, st>>>(G, d_insts, tol);
+        }
     };
-    bnorm_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    ++launches;
-    // graph capture: initial residual, then at most max_refine passes of
-    // (fast solve, update, residual, check) under device control
+    // graph capture: initial residual, the first kFixedPasses passes of (fast
+    // solve with the update fused, residual) as plain nodes (their kernels
+    // return at once after convergence), then the rest of the at most
+    // max_refine passes under device control. A warm-started solve mostly
+    // converges within the plain passes, and a loop that its opening kernel
+    // leaves closed costs less than loop iterations do.
     if (max_refine > 0 && stream_capturing(s, aux)) {
-        residual(s);
-        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, rblocks, 1, (int)blocks);
-        const bool looped = capture_while(s, aux, d_insts, [&](cudaStream_t b, cudaGraphConditionalHandle h) {
-            launch_fast_solve(G, d_insts, n_inst, b, tc_maps, tc_err);
-            update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, b>>>(G, d_insts);
-            residual(b);
-            check_kernel<<<n_inst, 256, 0, b>>>(d_insts, tol, rblocks, 0, (int)blocks);
-            launch_loop_ctl(d_insts, n_inst, max_refine, h, b);
-        });
-        if (!looped) return -1;
+        constexpr int kFixedPasses = 2;
+        const int fixed = std::min(max_refine, kFixedPasses);
+        residual(s, true);
+        for (int k = 0; k < fixed; ++k) {
+            launch_fast_solve(G, d_insts, n_inst, s, tc_maps, tc_err, true);
+            residual(s, false);
+        }
+        if (max_refine > fixed) {
+            const bool looped = capture_while(
+                s, aux, d_insts,
+                [&](cudaStream_t b, cudaGraphConditionalHandle h) {
+                    launch_fast_solve(G, d_insts, n_inst, b, tc_maps, tc_err, true);
+                    residual(b, false);
+                    launch_loop_ctl(d_insts, n_inst, max_refine, h, b);
+                },
+                n_inst, fixed, max_refine);
+            if (!looped) return -1;
+        }
         launch_esc(G, d_insts, n_inst, s);
-        return launches + 4;
+        return 3 + 4 * fixed;
     }
     for (int it = 0; it <= max_refine; ++it) {
-        residual(s);
-        check_kernel<<<n_inst, 256, 0, s>>>(d_insts, tol, rblocks, it == 0 ? 1 : 0, (int)blocks);
-        launches += 2;
-        if (it == max_refine) break;
-        launches += launch_fast_solve(G, d_insts, n_inst, s, tc_maps, tc_err);
-        update_kernel<<<dim3(blocks, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        residual(s, it == 0);
         launches += 1;
+        if (it == max_refine) break;
+        launches += launch_fast_solve(G, d_insts, n_inst, s, tc_maps, tc_err, true);
     }
     launch_esc(G, d_insts, n_inst, s);
     return launches + 1;

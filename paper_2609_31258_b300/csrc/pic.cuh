@@ -46,8 +46,8 @@ struct PicInst {
     int *conv;               // converged flag
     double *r64, *z64, *q64; // [M][Nu] PCG vectors (mask-aware solve) or NULL
     double *p64;             // [pnz][pnr] PCG search direction or NULL
-    double *part;            // [2][kRedBlocks] per-block partial sums (block-ordered reductions) or NULL
-    unsigned *ticket;        // arrival counter of those partial sums (zero between launches) or NULL
+    double *part;            // [2][kRedBlocks] per-block partial sums (block-ordered reductions)
+    unsigned *ticket;        // arrival counter of those partial sums (zero between launches)
 };
 
 // Tensor-core DST-I contractions (dst_tc.cu): every operand is a pair of
@@ -95,9 +95,10 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
                      int *tc_err = nullptr);
 // Maskless fast solve A d = r: r32 -> (DST-I, Thomas per mode, inverse DST-I) -> d32;
 // with tc_maps (the instances' descriptors, kTcMaps each) the residual comes
-// as rT and both contractions run on the tensor cores.
+// as rT and both contractions run on the tensor cores. With acc_phi the
+// correction is added to Phi (Phi[j+1][i] += d[j][i]) instead of stored.
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s,
-                      const CUtensorMap *tc_maps = nullptr, int *tc_err = nullptr);
+                      const CUtensorMap *tc_maps = nullptr, int *tc_err = nullptr, bool acc_phi = false);
 // C[m][n] = alpha sum_k A[m][k] B[n][k] per instance z (A: Mg x K, B: Ng x K,
 // K-major, each a TF32 pair of FP32 rows read by TMA through the descriptors
 // maps[z * kTcMaps + first .. + 3] = A_hi, A_lo, B_hi, B_lo), formed on the
@@ -129,14 +130,23 @@ int launch_pic_solve_masked(const PicGeom &G, const PicInst *d_insts, int n_inst
 // Device-controlled loop for a stream under capture: adds a while node after
 // the captured work of `s`, captures `body(aux)` as its body and lets the
 // capture of `s` continue after the node. The body must end with
-// launch_loop_ctl. Returns false when `s` is not being captured, `aux` is
-// null or a graph call fails (the capture is then unusable).
-template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body);
+// launch_loop_ctl. The condition starts at 1 (the body runs at least once)
+// after launch_loop_reset; with `done` >= 0 it starts at 0 and a kernel
+// captured before the node (launch_loop_open) opens the loop only while a
+// listed instance is unconverged and fewer than max_passes passes, counting
+// the `done` passes issued before the node, have run. Returns false when `s`
+// is not being captured, `aux` is null or a graph call fails (the capture is
+// then unusable).
+template <class Body>
+bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body, int n_inst = 0,
+                   int done = -1, int max_passes = 0);
 // Loop control of a captured while node: counts the passes (kept in the
 // first instance's red[7], cleared by launch_loop_reset before the node) and
 // continues while a listed instance is unconverged and fewer than max_passes
 // passes have run.
 void launch_loop_reset(const PicInst *d_insts, cudaStream_t s);
+void launch_loop_open(const PicInst *d_insts, int n_inst, int done, int max_passes, cudaGraphConditionalHandle h,
+                      cudaStream_t s);
 void launch_loop_ctl(const PicInst *d_insts, int n_inst, int max_passes, cudaGraphConditionalHandle h,
                      cudaStream_t s);
 
@@ -147,20 +157,29 @@ inline bool stream_capturing(cudaStream_t s, cudaStream_t aux)
     return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
 }
 
-template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body)
+template <class Body>
+bool capture_while(cudaStream_t s, cudaStream_t aux, const PicInst *d_insts, Body body, int n_inst, int done,
+                   int max_passes)
 {
     if (!stream_capturing(s, aux)) return false;
-    launch_loop_reset(d_insts, s);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return false;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, done >= 0 ? 0u : 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return false;
+    if (done >= 0)
+        launch_loop_open(d_insts, n_inst, done, max_passes, h, s);
+    else
+        launch_loop_reset(d_insts, s);
     const cudaGraphNode_t *deps = nullptr;
     size_t nd = 0;
     if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
         cs != cudaStreamCaptureStatusActive)
         return false;
     const std::vector<cudaGraphNode_t> dep(deps, deps + nd);
-    cudaGraphConditionalHandle h;
-    if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) return false;
     cudaGraphNodeParams p{};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
@@ -172,15 +191,14 @@ template <class Body> bool capture_while(cudaStream_t s, cudaStream_t aux, const
     if (cudaStreamBeginCaptureToGraph(aux, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return false;
     body(aux, h);
-    cudaGraph_t done = nullptr;
-    if (cudaStreamEndCapture(aux, &done) != cudaSuccess) return false;
+    cudaGraph_t fin = nullptr;
+    if (cudaStreamEndCapture(aux, &fin) != cudaSuccess) return false;
     return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
            cudaSuccess;
 }
 
-// E_SCE by central differences of Phi.
+// E_SCE by central differences of Phi, at the nodes (esc) and, for the
+// instances that have esc4, regrouped per cell.
 void launch_esc(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
-// E_SCE regrouped per cell (esc -> esc4) for the instances that have esc4.
-void launch_esc_cells(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s);
 
 } // namespace mucite

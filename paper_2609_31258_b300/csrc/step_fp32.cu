@@ -145,8 +145,19 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float4 c, float4 d, 
                        w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w);
 }
 
+// Per-lane cache of the last PIC cell read: its index and the E_SCE of its
+// four nodes (32 bytes, in two shared-memory slots of the lane). The field
+// is fixed for the length of a launch (the solve runs between launches) and
+// a pack crosses a PIC cell boundary only every few tens of micro steps, so
+// most steps read the cell from shared memory instead of L2. The values are
+// the same either way. cell = -1: empty; lo = nullptr: no cache.
+struct EscCache {
+    int cell;
+    float4 *lo, *hi;
+};
+
 __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float fx, float fy,
-                                       float rr, int32_t zq, Local &L)
+                                       float rr, int32_t zq, Local &L, EscCache *C = nullptr)
 {
     int i0, j0;
     float ar, az;
@@ -177,8 +188,21 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
         cell_r(rr * P.psr, P.pnr, pi0, pr);
         cell_z(zq, P.pnz, pj0, pz);
         // the cell's four nodes in one 32-byte sector
-        const float4 *e = P.esc4 + 2 * ((size_t)pj0 * (P.pnr - 1) + pi0);
-        const float4 lo = __ldg(&e[0]), hi = __ldg(&e[1]);
+        const int c = pj0 * (P.pnr - 1) + pi0;
+        float4 lo, hi;
+        if (C != nullptr && C->lo != nullptr && c == C->cell) {
+            lo = *C->lo;
+            hi = *C->hi;
+        } else {
+            const float4 *e = P.esc4 + 2 * (size_t)c;
+            lo = __ldg(&e[0]);
+            hi = __ldg(&e[1]);
+            if (C != nullptr && C->lo != nullptr) {
+                *C->lo = lo;
+                *C->hi = hi;
+                C->cell = c;
+            }
+        }
         const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
                     v11 = pr * pz;
         L.esr = v00 * lo.x + v10 * lo.z + v01 * hi.x + v11 * hi.z;
@@ -571,10 +595,10 @@ template <bool kExtras>
 __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
                                            uint32_t pack, float fx, float fy, float rr, int32_t zq,
                                            float &vx, float &vy, float &vz, float &tau, float &t,
-                                           float &w, bool &lv, StepGas &S)
+                                           float &w, bool &lv, StepGas &S, EscCache &C)
 {
     Local L;
-    gather(G, P, fx, fy, rr, zq, L);
+    gather(G, P, fx, fy, rr, zq, L, &C);
     kick_of(P, L, s_rf[2 * k], S.kx, S.ky, S.kz);
     S.nsig = L.nsig; S.T = L.T;
     S.ux = L.ux; S.uy = L.uy; S.uz = L.uz;
@@ -602,7 +626,7 @@ __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, c
 // do not depend on the schedule.
 template <bool kExtras>
 __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P, const float *s_rf,
-                                              int64_t off, int nsteps)
+                                              int64_t off, int nsteps, float4 *s_esc)
 {
     const int64_t p = off + threadIdx.x;
     const bool owned = p < P.n_slots && P.status[p] == MUCITE_ACTIVE;
@@ -624,7 +648,12 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
     float t = 0.0f, w = 0.0f;
     bool lv = false, live = owned && nsteps > 0, pend = false;
     StepGas S;
-    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S);
+    EscCache C{-1, nullptr, nullptr};
+    if (s_esc != nullptr && P.esc4 != nullptr) {
+        C.lo = s_esc + threadIdx.x;
+        C.hi = s_esc + blockDim.x + threadIdx.x;
+    }
+    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S, C);
     for (;;) {
         const bool can_push = live && !pend;
         const unsigned mc = __ballot_sync(0xffffffffu, pend);
@@ -656,7 +685,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
             if (st != MUCITE_ACTIVE || k == nsteps)
                 live = false;
             else
-                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S);
+                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S, C);
         }
     }
     if (owned) {
@@ -792,9 +821,12 @@ template <bool kCollide, bool kExtras, int kMinBlocks>
 __global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
     step_f32_kernel(GridF32 G, const InstF32 *insts,
                                                        const int32_t *tile_start, int n_inst,
-                                                       int total_tiles, int nsteps)
+                                                       int total_tiles, int nsteps, int esc_cache)
 {
-    extern __shared__ float s_rf[];
+    // dynamic shared memory: the RF scalars of the launch, then (esc_cache)
+    // the per-lane PIC cell caches of the collision tiles
+    extern __shared__ __align__(16) float s_rf[];
+    float4 *s_esc = esc_cache ? reinterpret_cast<float4 *>(s_rf + ((2 * nsteps + 1 + 3) & ~3)) : nullptr;
     __shared__ __align__(16) unsigned char p_raw[sizeof(InstF32)];
     const InstF32 &P = *reinterpret_cast<const InstF32 *>(p_raw);
     int cur = -1;
@@ -818,7 +850,7 @@ __global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
         constexpr int kU = kCollide ? 1 : kFreeU;
         const int64_t off = (int64_t)(t - __ldg(&tile_start[lo])) * (kU * blockDim.x);
         if (kCollide)
-            run_tile_coll<kExtras>(G, P, s_rf, off, nsteps);
+            run_tile_coll<kExtras>(G, P, s_rf, off, nsteps, s_esc);
         else
             run_tile_free<kExtras, kU>(G, P, s_rf, off, nsteps);
     }
@@ -992,31 +1024,40 @@ static bool wide_gather(const GridF32 &G)
 
 // kCollide: the collision code is compiled in; kExtras: dissociation (Eq. 7)
 // and the hybrid Langevin branch are compiled in.
+// Dynamic shared memory of a step launch: the 2 nsteps + 1 RF scalars
+// (padded to 16 bytes), then with esc_cache two float4 per thread.
+static size_t step_f32_smem(int threads, int nsteps, bool esc_cache)
+{
+    const size_t rf = sizeof(float) * (size_t)((2 * nsteps + 1 + 3) & ~3);
+    return rf + (esc_cache ? 2 * sizeof(float4) * (size_t)threads : 0);
+}
+
 void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_start, int n_inst,
                      int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
-                     cudaStream_t s)
+                     bool esc_cache, cudaStream_t s)
 {
     rf_table_kernel<<<n_inst, 128, 0, s>>>(d_insts, nsteps);
-    const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
+    const int ec = esc_cache && collide ? 1 : 0;
+    const size_t smem = step_f32_smem(threads, nsteps, ec != 0);
     const bool wide = wide_gather(G);
     if (collide && extras && wide)
         step_f32_kernel<true, true, 3><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
-                                                                   nsteps);
+                                                                   nsteps, ec);
     else if (collide && extras)
         step_f32_kernel<true, true, 4><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
-                                                                   nsteps);
+                                                                   nsteps, ec);
     else if (collide && wide)
         step_f32_kernel<true, false, 3><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
-                                                                    nsteps);
+                                                                    nsteps, ec);
     else if (collide)
         step_f32_kernel<true, false, 4><<<grid, threads, smem, s>>>(G, d_insts, d_tile_start, n_inst, total_tiles,
-                                                                    nsteps);
+                                                                    nsteps, ec);
     else if (extras)
         step_f32_kernel<false, true, 6><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
-                                                                              total_tiles, nsteps);
+                                                                              total_tiles, nsteps, ec);
     else
         step_f32_kernel<false, false, 6><<<grid, threads / kFreeU, smem, s>>>(G, d_insts, d_tile_start, n_inst,
-                                                                               total_tiles, nsteps);
+                                                                               total_tiles, nsteps, ec);
 }
 
 void launch_step_f32_stream(const GridF32 &G, const InstF32 &P, InstF32 *d_insts, int total_tiles, int grid,
@@ -1037,10 +1078,10 @@ void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t
     advance_clock_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(d_insts, n_inst, nsteps);
 }
 
-int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras)
+int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras, bool esc_cache)
 {
     int b = 0;
-    const size_t smem = sizeof(float) * (size_t)(2 * nsteps + 1);
+    const size_t smem = step_f32_smem(threads, nsteps, esc_cache && collide);
     const bool wide = wide_gather(G);
     if (collide && extras)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
