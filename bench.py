@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ion-pack steps/s (FP32 batched vs plain FP64, same GPU); p50/p99 request latency"
 UNIT = "pack-steps/s"
+FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of a B300
 
 
 def _peaks():
@@ -611,7 +612,7 @@ def main():
     ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "all"],
                     help="batch policy of the serving loop")
     ap.add_argument("--section", default="all",
-                    choices=["all", "fused", "streamed", "serving", "sweep", "space_charge", "paper_grid"],
+                    choices=["all", "fused", "streamed", "serving", "sweep", "space_charge", "paper_grid", "fp64"],
                     help="run only one timed section (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -644,6 +645,13 @@ def main():
         build.build()
         dev = torch.device("cuda", local)
         print(json.dumps(_sweep(args, local, torch.cuda.Stream(dev), dev)))
+        return
+    if args.section == "fp64":
+        torch.cuda.set_device(local)
+        build.build()
+        dev = torch.device("cuda", local)
+        w = W.ring_stack(n_packs=args.packs, n_steps=0, seed=1 + rank, precision=0)
+        print(json.dumps(_fp64(args, w, local, torch.cuda.Stream(dev), dev)))
         return
     if args.section == "streamed":
         torch.cuda.set_device(local)
@@ -1165,8 +1173,21 @@ def _fp64(args, w32, local, stream, dev):
     ms = a.elapsed_time(b)
     ps = T1["pack_steps"] - T0["pack_steps"]
     ctx.close()
-    return {"value": ps / (ms * 1e-3), "unit": UNIT, "micro_steps_timed": micro * args.fp64_steps,
-            "ms": ms, "note": "one launch per micro step, FP64 state and fields"}
+    value = ps / (ms * 1e-3)
+    # FP64 rate of the plain step: FP64 flops per pack-step (DADD + DMUL +
+    # 2 DFMA, counted by ncu on the same launch) times the measured rate,
+    # against the part's nominal FP64 peak (null once the kernel's sources
+    # change after the summary was taken)
+    prof, stale = _profile_fields("step_f64_ring_stack.txt", "step_fp64.cu")
+    fpp = None if stale or "fp64_flop_per_pack_step" not in prof else float(prof["fp64_flop_per_pack_step"])
+    ach = fpp * value / 1e9 if fpp else None
+    roof = {"bound": "fp64", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": ach / FP64_PEAK_GFLOPS if ach else None, "peak_source": "nominal B300 FP64 (no measured figure)",
+            "fp64_flop_per_pack_step": fpp,
+            "fp64_pipe_active": prof.get("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active") if not stale else None,
+            "profile_stale": stale}
+    return {"value": value, "unit": UNIT, "micro_steps_timed": micro * args.fp64_steps,
+            "ms": ms, "note": "one launch per micro step, FP64 state and fields", "roofline": roof}
 
 
 if __name__ == "__main__":
