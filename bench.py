@@ -188,7 +188,7 @@ def cpu_baseline_run(n_packs=100_000, min_seconds=10.0, max_micro=20000, w=None)
     dt = time.perf_counter() - t0
     ps = int(s.nsteps.sum()) - n0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
             "sample": f"{n_packs} packs x {done} micro steps of the same 512x2048 ring-stack workload "
                       f"({ps} pack-steps in {dt:.1f} s, FP64 C oracle, OpenMP over packs)"}
 
@@ -551,21 +551,24 @@ def run_reference(args):
         return
     from paper_2609_31258_b300 import workloads as W
     w = W.ring_stack(n_packs=args.packs, n_steps=0, precision=1)
-    steps = []
+    steps, secs = [], []
     cb = None
     for k in range(args.warmup + args.steps):
         # each step a bounded sample (about 8 s) of the same workload
         r = cpu_baseline_run(n_packs=args.packs, min_seconds=8.0, max_micro=args.micro, w=w)
         if k >= args.warmup:
             steps.append(r["value"])
+            secs.append(r["seconds"])
             cb = r
     val = sum(steps) / len(steps)
+    # wall time of one timed (sampled) step
+    ms_step = 1e3 * sum(secs) / len(secs)
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _config(args, w.name, ws),
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                            "sample": cb["sample"]},
+                            "sample": "each timed step: " + cb["sample"]},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
