@@ -214,6 +214,8 @@ void free_instance(Instance &I)
     dfree(I.d_tsum);
     dfree(I.pic.Q);
     dfree(I.pic.phi);
+    dfree(I.pic.phi_prev);
+    dfree(I.pic.phi_hist);
     dfree(I.pic.r32);
     dfree(I.pic.hat);
     dfree(I.tc_rT);
@@ -1185,6 +1187,10 @@ mucite_status mucite_inject(mucite_ctx *ctx, int instance, const mucite_ion_temp
         const size_t nn = (size_t)G.pnr * G.pnz, nu = (size_t)G.M * G.Nu;
         CK(cudaMalloc(&I.pic.Q, nn * sizeof(unsigned long long)));
         CK(cudaMalloc(&I.pic.phi, nn * sizeof(double)));
+        CK(cudaMalloc(&I.pic.phi_prev, nn * sizeof(double)));
+        CK(cudaMalloc(&I.pic.phi_hist, sizeof(int)));
+        CK(cudaMemsetAsync(I.pic.phi_prev, 0, nn * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(I.pic.phi_hist, 0, sizeof(int), ctx->stream));
         CK(cudaMalloc(&I.pic.r32, nu * sizeof(float)));
         CK(cudaMalloc(&I.pic.hat, (size_t)G.Nu * G.hld * sizeof(float)));
         CK(cudaMalloc(&I.pic.d32, nu * sizeof(float)));
@@ -1367,7 +1373,8 @@ size_t pic_state_bytes(const mucite_ctx *ctx)
 {
     const size_t nn = (size_t)ctx->pg.pnr * ctx->pg.pnz;
     const size_t nc = (size_t)(ctx->pg.pnr - 1) * (ctx->pg.pnz - 1);
-    return nn * (sizeof(unsigned long long) + sizeof(double) + sizeof(float2)) + nc * 2 * sizeof(float4);
+    return nn * (sizeof(unsigned long long) + 2 * sizeof(double) + sizeof(float2)) + nc * 2 * sizeof(float4) +
+           256;
 }
 
 mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
@@ -1400,6 +1407,9 @@ mucite_status snapshot_take(mucite_ctx *ctx, Snapshot &S)
             CK(cudaMemcpyAsync(q + nn * 16, I->pic.esc, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             if (I->pic.esc4)
                 CK(cudaMemcpyAsync(q + nn * 24, I->pic.esc4, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
+            char *h = q + nn * 24 + nc * 32;
+            CK(cudaMemcpyAsync(h, I->pic.phi_prev, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(h + nn * 8, I->pic.phi_hist, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
         }
         CK(cudaMemcpyAsync(&S.counters[kCounters * k], I->d_counters, kCounters * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, ctx->stream));
@@ -1423,6 +1433,9 @@ mucite_status snapshot_restore(mucite_ctx *ctx, const Snapshot &S)
             CK(cudaMemcpyAsync(I->pic.esc, q + nn * 16, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             if (I->pic.esc4)
                 CK(cudaMemcpyAsync(I->pic.esc4, q + nn * 24, nc * 32, cudaMemcpyDeviceToDevice, ctx->stream));
+            const char *h = q + nn * 24 + nc * 32;
+            CK(cudaMemcpyAsync(I->pic.phi_prev, h, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(I->pic.phi_hist, h + nn * 8, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
         }
         CK(cudaMemcpyAsync(I->d_counters, &S.counters[kCounters * k], kCounters * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, ctx->stream));

@@ -213,15 +213,31 @@ __global__ void __launch_bounds__(256) deposit_kernel(const DepositArgs *args, c
     }
 }
 
+// Start of a warm-started solve: with phi_prev, Phi_n = 2 Phi_{n-1} - Phi_{n-2}
+// (the last two solutions extrapolated linearly in time; from the second
+// solve on) and phi_prev <- Phi_{n-1}. Any start converges to the same
+// tolerance; this one leaves the first correction a smaller residual, the
+// charge moving steadily between updates.
+__device__ __forceinline__ void start_phi(const PicInst &I, int64_t e, bool ext)
+{
+    if (I.phi_prev == nullptr) return;
+    const double p = I.phi[e];
+    if (ext) I.phi[e] = 2.0 * p - I.phi_prev[e];
+    I.phi_prev[e] = p;
+}
+
 // Clears the node charges and the convergence bookkeeping of every instance
-// before a macro step (blockIdx.y = instance).
+// before a macro step (blockIdx.y = instance); the start of the solve.
 __global__ void __launch_bounds__(256) pic_prepare_kernel(PicGeom G, const PicInst *insts)
 {
     const PicInst &I = insts[blockIdx.y];
     const int64_t n = (int64_t)G.pnr * G.pnz;
+    const bool ext = I.phi_prev != nullptr && *I.phi_hist != 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x)
+         e += (int64_t)gridDim.x * blockDim.x) {
         I.Q[e] = 0ull;
+        start_phi(I, e, ext);
+    }
     if (blockIdx.x == 0 && threadIdx.x < 8) I.red[threadIdx.x] = 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
 }
@@ -230,10 +246,12 @@ __global__ void __launch_bounds__(256) pic_take_kernel(PicGeom G, const PicInst 
 {
     const PicInst &I = insts[blockIdx.y];
     const int64_t n = (int64_t)G.pnr * G.pnz;
+    const bool ext = I.phi_prev != nullptr && *I.phi_hist != 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         I.Q[e] = I.Qn[e];
         I.Qn[e] = 0ull;
+        start_phi(I, e, ext);
     }
     if (blockIdx.x == 0 && threadIdx.x < 8) I.red[threadIdx.x] = 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *I.conv = 0;
@@ -638,54 +656,6 @@ __global__ void __launch_bounds__(256) thomas_smem_kernel(PicGeom G, const PicIn
     }
 }
 
-// Tridiagonal solve of one axial mode k per block by parallel cyclic
-// reduction: row i of mode k reads a_i x_{i-1} + d_ik x_i + c_i x_{i+1} = h_i
-// with d_ik = -(a_i + c_i + A_i lambda_k), lambda_k = 4 sin^2(pi k / (2 (M+1)))
-// (the z eigenvalue of mode k; x_Nu = 0 at the outer radius). Every round
-// eliminates the couplings to the rows at distance s (s = 1, 2, 4, ...) from
-// each row with the rows at distance s, so after ceil(log2 Nu) rounds each
-// row stands alone: x_i = d_i / b_i. One thread per row (Nu <= 256), rows
-// past Nu are identity rows; the rounds run on shared memory, so the solve
-// costs 8 short rounds instead of a dependent chain of 2 Nu steps. The
-// systems are diagonally dominant, where cyclic reduction is stable.
-__global__ void __launch_bounds__(256) pcr_kernel(PicGeom G, const PicInst *insts)
-{
-    __shared__ float sa[2][256], sb[2][256], sc[2][256], sd[2][256];
-    const PicInst &I = insts[blockIdx.z];
-    if (*I.conv) return;
-    const int k = blockIdx.x, i = threadIdx.x, n = G.Nu;
-    const float sn = sinpif((float)(k + 1) / (2.0f * (float)(G.M + 1)));
-    const float lam = 4.0f * sn * sn;
-    float a = 0.0f, b = 1.0f, c = 0.0f, d = 0.0f;
-    if (i < n) {
-        const float ai = (float)G.a[i], ci = (float)G.c[i];
-        a = ai; // a_0 = 0: no flux through the axis
-        c = i + 1 < n ? ci : 0.0f;
-        b = -(ai + ci + (float)G.A[i] * lam);
-        d = I.hat[(size_t)i * G.hld + k];
-    }
-    int cur = 0;
-    sa[0][i] = a; sb[0][i] = b; sc[0][i] = c; sd[0][i] = d;
-    __syncthreads();
-    for (int st = 1; st < n; st <<= 1) {
-        const int lo = i - st, hi = i + st;
-        const bool hl = lo >= 0, hh = hi < 256;
-        const float am = hl ? sa[cur][lo] : 0.0f, bm = hl ? sb[cur][lo] : 1.0f;
-        const float cm = hl ? sc[cur][lo] : 0.0f, dm = hl ? sd[cur][lo] : 0.0f;
-        const float ap = hh ? sa[cur][hi] : 0.0f, bp = hh ? sb[cur][hi] : 1.0f;
-        const float cp = hh ? sc[cur][hi] : 0.0f, dp = hh ? sd[cur][hi] : 0.0f;
-        const float al = -__fdividef(a, bm), ga = -__fdividef(c, bp);
-        b = b + al * cm + ga * ap;
-        d = d + al * dm + ga * dp;
-        a = al * am;
-        c = ga * cp;
-        cur ^= 1;
-        sa[cur][i] = a; sb[cur][i] = b; sc[cur][i] = c; sd[cur][i] = d;
-        __syncthreads();
-    }
-    if (i < n) store_hat(I, (size_t)i * G.hld + k, __fdividef(d, b));
-}
-
 // Tridiagonal solve per axial mode k, in place on hat[i][k] (i = 0..Nu-1),
 // with the elimination factors of the fixed operator precomputed.
 __global__ void __launch_bounds__(256) thomas_kernel(PicGeom G, const PicInst *insts)
@@ -743,6 +713,7 @@ __global__ void __launch_bounds__(256) esc_kernel(PicGeom G, const PicInst *inst
     __syncthreads();
     const double idr = rcp[0], i2dr = rcp[1], idz = rcp[2], i2dz = rcp[3];
     const PicInst &I = insts[blockIdx.z];
+    if (I.phi_hist != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *I.phi_hist = 1; // Phi is solved
     const int lw = row_shift(G.pnr), per = 256 >> lw;
     const int sub = threadIdx.x >> lw, t = threadIdx.x & ((1 << lw) - 1);
     const int cr = G.pnr - 1, cz = G.pnz - 1;
@@ -824,18 +795,29 @@ void launch_sym(void (*kern)(PicGeom, const PicInst *, int, float), dim3 grid, i
     cudaLaunchKernelEx(&cfg, kern, G, d_insts, splits, alpha);
 }
 
+// Radial tridiagonal solves of every axial mode: the 8-mode blocks on
+// shared memory up to kThRows radial unknowns, the global-memory sweep
+// above. Both run the Thomas recurrences with the elimination factors formed
+// in FP64 (stored in FP32): in FP32 they leave the correction accurate
+// enough that a warm-started solve on 256 x 1024 meets 1e-6 after one pass
+// (residual about 2e-7), where parallel cyclic reduction, faster per call
+// but with its eliminations rounded in FP32 at every level, left 1e-5 and
+// needed a second pass.
+void launch_thomas(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s)
+{
+    if (G.Nu <= kThRows)
+        thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    else
+        thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+}
+
 int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cudaStream_t s,
                       const CUtensorMap *tc_maps, int *tc_err, bool acc_phi)
 {
     if (tc_maps != nullptr) {
         // hat[i][k] = 2/(M+1) sum_j rT[i][j] S[k][j]  (S symmetric)
         launch_dst_tc(tc_maps, 0, d_insts, n_inst, true, G, (float)(2.0 / (G.M + 1)), tc_err, s);
-        if (G.Nu > 128 && G.Nu <= 256)
-            pcr_kernel<<<dim3(G.M, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        else if (G.Nu <= kThRows)
-            thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
-        else
-            thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+        launch_thomas(G, d_insts, n_inst, s);
         // d32[j][i] = sum_k S[j][k] hat[i][k]
         launch_dst_tc(tc_maps, 4, d_insts, n_inst, false, G, 1.0f, tc_err, s);
         if (!acc_phi) return 3;
@@ -853,16 +835,7 @@ int launch_fast_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, cuda
     const dim3 gi((unsigned)(((G.Nu + 63) / 64) * splits), (H + 63) / 64, n_inst);
     // hat[i][k] = 2/(M+1) sum_j r32[j][i] S[j][k]
     launch_sym(dst_sym_kernel<false>, gf, splits, G, d_insts, (float)(2.0 / (G.M + 1)), s);
-    // radial systems of 129..256 unknowns: cyclic reduction (a long Thomas
-    // chain); up to 128 the 8-mode Thomas blocks are as fast and more
-    // accurate in FP32. The choice depends on the grid only, so batched and
-    // single-instance solves of the same grid take the same arithmetic.
-    if (G.Nu > 128 && G.Nu <= 256)
-        pcr_kernel<<<dim3(G.M, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    else if (G.Nu <= kThRows)
-        thomas_smem_kernel<<<dim3((G.M + kThModes - 1) / kThModes, 1, n_inst), 256, 0, s>>>(G, d_insts);
-    else
-        thomas_kernel<<<dim3((G.M + 255) / 256, 1, n_inst), 256, 0, s>>>(G, d_insts);
+    launch_thomas(G, d_insts, n_inst, s);
     // d32[j][i] = sum_k S[j][k] hat[i][k], or Phi[j+1][i] += that
     launch_sym(acc_phi ? dst_sym_kernel<true, true> : dst_sym_kernel<true, false>, gi, splits, G, d_insts, 1.0f,
                s);
@@ -939,10 +912,10 @@ int launch_pic_solve(const PicGeom &G, const PicInst *d_insts, int n_inst, int m
     // solve with the update fused, residual) as plain nodes (their kernels
     // return at once after convergence), then the rest of the at most
     // max_refine passes under device control. A warm-started solve mostly
-    // converges within the plain passes, and a loop that its opening kernel
+    // converges within the plain pass, and a loop that its opening kernel
     // leaves closed costs less than loop iterations do.
     if (max_refine > 0 && stream_capturing(s, aux)) {
-        constexpr int kFixedPasses = 2;
+        constexpr int kFixedPasses = 1;
         const int fixed = std::min(max_refine, kFixedPasses);
         residual(s, true);
         for (int k = 0; k < fixed; ++k) {

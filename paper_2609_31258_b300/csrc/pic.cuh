@@ -30,6 +30,9 @@ struct PicInst {
     unsigned long long *Qn;  // [pnz][pnr] charge deposited by the step kernels at the end of a macro
                              // step's launch, taken over by the next solve (FP32 graph replays) or NULL
     double *phi;             // [pnz][pnr] potential (zero on the Dirichlet boundary)
+    double *phi_prev;        // [pnz][pnr] Phi of the update before, for the extrapolated start of a
+                             // warm-started solve, or NULL (start from the last Phi)
+    int *phi_hist;           // nonzero once phi_prev holds a solved Phi (set by esc_kernel)
     float *r32;              // [M][Nu] residual in FP32
     float *hat;              // [Nu][hld] transformed residual / correction
     float *hat_lo;           // [Nu][hld] with the tensor-core contractions: the tridiagonal solves write
