@@ -276,8 +276,9 @@ mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, 
  * of e * 2^-30 -> finite-volume cylindrical Poisson (dPhi/dr = 0 on the
  * axis, Phi = 0 at both axial ends and at r = R) solved by an FP32 DST-I in z
  * with a tridiagonal solve per mode, refined in FP64 until
- * ||b - A Phi|| / ||b|| <= 1e-6 (at most 4 correction passes, warm-started
- * from the previous solution; one or two suffice on the config workloads, and
+ * ||b - A Phi|| / ||b|| <= 1e-6 (at most 4 correction passes, started from
+ * the last two solutions extrapolated linearly in time, 2 Phi_{n-1} -
+ * Phi_{n-2}; one pass suffices in steady state on the config workloads, and
  * mucite_pic_read reports the residual reached and the passes taken) -> E_SCE
  * by central differences on the PIC grid.
  * Errors: MUCITE_E_STATE (no PIC grid or instance), MUCITE_E_CUDA. */
