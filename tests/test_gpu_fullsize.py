@@ -77,3 +77,35 @@ def test_space_charge_full_size_deposit_and_solve(orc):
     assert got["rel_residual"] <= 1e-6 and res <= 1e-6, (got["rel_residual"], res)
     assert abs(res - got["rel_residual"]) <= 1e-3 * res + 1e-12, (got["rel_residual"], res)
     ctx.close()
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_space_charge_every_update_meets_tolerance(orc, graphs):
+    """Cylinder with space charge at the benchmark's size (1e6 packs, 256 x
+    1024 PIC grid every 10 micro steps), 300 micro steps: every warm-started
+    solve that can be read back -- each update when issued directly, the
+    second of every two when two macro steps are replayed as graphs -- meets
+    the paper's 1e-6 tolerance, on the residual the library reports and on the
+    oracle's FP64 recomputation from the returned potential and charge. The
+    solves start from the last two solutions extrapolated in time and take one
+    correction pass once that start exists (at most two at any update)."""
+    import torch
+    from oracle import poisson
+    from paper_2609_31258_b300 import build, mucite
+    build.build()
+    w = W.cylinder_space_charge(n_packs=1_000_000, n_steps=0, precision=0)
+    ctx = mucite.Context(0, torch.cuda.Stream())
+    ctx.set_launch_mode(0, graphs)
+    mucite.load_workload(ctx, w, 0)
+    per_call = 20 if graphs else 10
+    passes = []
+    for call in range(300 // per_call):
+        ctx.step(0, per_call)
+        got = ctx.pic_read(0)
+        res = poisson.residual(w.fields.pic, got["Q"], got["phi"])
+        assert got["rel_residual"] <= 1e-6 and res <= 1e-6, (call, got["rel_residual"], res)
+        assert abs(res - got["rel_residual"]) <= 1e-3 * res + 1e-12, (call, got["rel_residual"], res)
+        passes.append(got["iterations"])
+    ctx.close()
+    assert max(passes[2:]) <= 2, passes
+    assert sum(p == 1 for p in passes[2:]) >= 0.8 * len(passes[2:]), passes
