@@ -16,9 +16,10 @@ from helpers import fp32_state_from_oracle, upload
 pytestmark = pytest.mark.gpu
 
 
-# 65 x 257: shared-memory Thomas sweeps; 150 x 257: cyclic reduction; 256 x
-# 1024 (the largest size the scratch holds, the benchmark's grid): cyclic
-# reduction and the DST-I contractions split over an 8-CTA cluster
+# 65 x 257 and 150 x 257: shared-memory Thomas sweeps of up to 64 and 149
+# radial unknowns; 256 x 1024 (the largest size the scratch holds, the
+# benchmark's grid): 255 radial unknowns and the DST-I contractions split over
+# an 8-CTA cluster
 @pytest.mark.parametrize("shape", [(65, 257), (150, 257), (256, 1024)])
 def test_noalloc_solve_matches_pic_update_twice(orc, shape):
     import torch
