@@ -112,10 +112,16 @@ struct Local {
 __device__ __forceinline__ void field_kick(const Local &L, float a, float dc, float srf, float &kx, float &ky,
                                            float &kz)
 {
-    const float kr = a * (dc * L.edr + srf * L.err + L.esr);
-    kx = kr * L.cx;
-    ky = kr * L.cy;
-    kz = a * (dc * L.edz + srf * L.erz + L.esz);
+    // (r, z) side by side in packed FP32x2 instructions:
+    // k_rz = a ((dc E_DC + srf E_RF) + E_SCE), then (kx, ky) = k_r (cx, cy)
+    float2 t = __fmul2_rn(make_float2(dc, dc), make_float2(L.edr, L.edz));
+    t = __ffma2_rn(make_float2(srf, srf), make_float2(L.err, L.erz), t);
+    t = __fadd2_rn(t, make_float2(L.esr, L.esz));
+    t = __fmul2_rn(make_float2(a, a), t);
+    const float2 kxy = __fmul2_rn(make_float2(t.x, t.x), make_float2(L.cx, L.cy));
+    kx = kxy.x;
+    ky = kxy.y;
+    kz = t.y;
 }
 
 // Cell index and fraction along one axis; clamped to the last cell.
@@ -136,13 +142,23 @@ __device__ __forceinline__ void cell_z(int32_t zq, int n, int &j0, float &f)
     f = j < 0 ? 0.0f : (j > n - 2 ? 1.0f : fr);
 }
 
+// Bilinear combination of four node records, each component summed in the
+// order w00 a + w10 b + w01 c + w11 d (a product, then three fused
+// multiply-adds), two components per packed FP32x2 instruction.
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float4 c, float4 d, float w00, float w10,
                                         float w01, float w11)
 {
-    return make_float4(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
-                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y,
-                       w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z,
-                       w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w);
+    const float2 p00 = make_float2(w00, w00), p10 = make_float2(w10, w10);
+    const float2 p01 = make_float2(w01, w01), p11 = make_float2(w11, w11);
+    float2 lo = __fmul2_rn(p00, make_float2(a.x, a.y));
+    float2 hi = __fmul2_rn(p00, make_float2(a.z, a.w));
+    lo = __ffma2_rn(p10, make_float2(b.x, b.y), lo);
+    hi = __ffma2_rn(p10, make_float2(b.z, b.w), hi);
+    lo = __ffma2_rn(p01, make_float2(c.x, c.y), lo);
+    hi = __ffma2_rn(p01, make_float2(c.z, c.w), hi);
+    lo = __ffma2_rn(p11, make_float2(d.x, d.y), lo);
+    hi = __ffma2_rn(p11, make_float2(d.z, d.w), hi);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // Per-lane cache of the last PIC cell read: its index and the E_SCE of its
@@ -484,11 +500,20 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
         yq += lattice_step(uy * P.cxs, dither(h2, 11));
         zq += lattice_step(uz * P.czs, dither(h2, 22));
     } else {
-        vx = add_sr(vx, kx, dither_c(h1, 0));
-        vy = add_sr(vy, ky, dither_c(h1, 11));
+        // x and y side by side in packed FP32x2 instructions (the same
+        // operations per component as add_sr and lattice_step)
+        const float2 v = make_float2(vx, vy), d = make_float2(kx, ky);
+        const float2 t = __fadd2_rn(v, d);
+        const float2 ulp = __fmul2_rn(make_float2(__int_as_float(__float_as_int(t.x) & 0x7f800000),
+                                                  __int_as_float(__float_as_int(t.y) & 0x7f800000)),
+                                      make_float2(1.1920928955078125e-7f, 1.1920928955078125e-7f));
+        const float2 nv = __fadd2_rn(v, __ffma2_rn(make_float2(dither_c(h1, 0), dither_c(h1, 11)), ulp, d));
+        vx = nv.x;
+        vy = nv.y;
         vz = add_sr(vz, kz, dither_c(h1, 22));
-        xq += lattice_step(vx * P.cxs, dither(h2, 0));
-        yq += lattice_step(vy * P.cxs, dither(h2, 11));
+        const float2 sxy = __fmul2_rn(nv, make_float2(P.cxs, P.cxs));
+        xq += lattice_step(sxy.x, dither(h2, 0));
+        yq += lattice_step(sxy.y, dither(h2, 11));
         zq += lattice_step(vz * P.czs, dither(h2, 22));
     }
     fx = (float)xq;
