@@ -277,8 +277,10 @@ __device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &
                                                float vz, float &tau, float &t, float &w)
 {
     const float cbar = 1.1283791670955126f * S.s; // 2 s / sqrt(pi)
-    const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
-    w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
+    const float wz = vz - S.uz;
+    const float2 sq = __fmul2_rn(wxy, wxy);
+    w = sqrt_fast(fmaf(wz, wz, sq.x + sq.y));
     const float nu = S.nsig * (w + cbar);
     const float room = nu * (P.dt - t);
     if (tau >= room) {
@@ -301,7 +303,10 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
 {
     const float s = S.s;
     const float cbar = 1.1283791670955126f * s;
-    const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
+    // x and y of the vector arithmetic side by side in packed FP32x2
+    // instructions (the same operations per component)
+    const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
+    const float wz = vz - S.uz;
     uint4 A = make_uint4(pack, step, 2u * kc, 0u), B = make_uint4(pack, step, 2u * kc + 1u, 0u);
     philox10x2(A, B, P.key0, P.key1);
     tau = -__logf(u22(B.z, B.w));
@@ -316,22 +321,26 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     }
     const float y = -__logf(u21(A.w)) - __logf(u21(B.x)) * f;
     const float cmag = s * sqrt_fast(y);
-    float cx, cy, cz;
+    float2 cxy;
+    float cz;
     {
         const float ct = 2.0f * u21(B.y) - 1.0f;
         const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
         float sn, cs;
         sincos_2pi(u21(B.z), sn, cs);
-        cx = cmag * st * cs;
-        cy = cmag * st * sn;
+        const float cst = cmag * st;
+        cxy = __fmul2_rn(make_float2(cst, cst), make_float2(cs, sn));
         cz = cmag * ct;
     }
-    const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
-    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float2 gxy = __fadd2_rn(wxy, make_float2(-cxy.x, -cxy.y));
+    const float gz = wz - cz;
+    const float2 gg = __fmul2_rn(gxy, gxy);
+    const float g2 = fmaf(gz, gz, gg.x + gg.y);
     const float g = sqrt_fast(g2);
     if (!(u21(A.y) * (w + cmag) < g)) return 0;
-    const float Vx = P.fM * vx + P.fm * (S.ux + cx);
-    const float Vy = P.fM * vy + P.fm * (S.uy + cy);
+    const float2 Vxy = __ffma2_rn(make_float2(P.fM, P.fM), make_float2(vx, vy),
+                                  __fmul2_rn(make_float2(P.fm, P.fm),
+                                             __fadd2_rn(make_float2(S.ux, S.uy), cxy)));
     const float Vz = P.fM * vz + P.fm * (S.uz + cz);
     const float etr = P.mu_2kb * g2;
     const float ec = etr + eint;
@@ -347,8 +356,10 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
     float sn, cs;
     sincos_2pi(u22(A.x, A.y), sn, cs);
-    vx = Vx + gn * st * cs;
-    vy = Vy + gn * st * sn;
+    const float gst = gn * st;
+    const float2 nv = __ffma2_rn(make_float2(gst, gst), make_float2(cs, sn), Vxy);
+    vx = nv.x;
+    vy = nv.y;
     vz = Vz + gn * ct;
     return 1;
 }
