@@ -184,19 +184,23 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     const float4 a01 = __ldg(&nd[G.nr].a), a11 = __ldg(&nd[G.nr + 1].a);
     const float4 b00 = __ldg(&nd[0].b), b10 = __ldg(&nd[1].b);
     const float4 b01 = __ldg(&nd[G.nr].b), b11 = __ldg(&nd[G.nr + 1].b);
-    const float w00 = (1.0f - ar) * (1.0f - az), w10 = ar * (1.0f - az);
-    const float w01 = (1.0f - ar) * az, w11 = ar * az;
-    const float4 fa = lerp4(a00, a10, a01, a11, w00, w10, w01, w11);
-    const float4 fb = lerp4(b00, b10, b01, b11, w00, w10, w01, w11);
+    // weights (w00, w10) and (w01, w11): (1 - ar, ar) times 1 - az and az
+    const float2 wr = make_float2(1.0f - ar, ar);
+    const float2 wl = __fmul2_rn(wr, make_float2(1.0f - az, 1.0f - az));
+    const float2 wh = __fmul2_rn(wr, make_float2(az, az));
+    const float4 fa = lerp4(a00, a10, a01, a11, wl.x, wl.y, wh.x, wh.y);
+    const float4 fb = lerp4(b00, b10, b01, b11, wl.x, wl.y, wh.x, wh.y);
     const float inv = rr > 0.0f ? __fdividef(1.0f, rr) : 0.0f;
-    const float cx = fx * inv, cy = fy * inv; // Eq. 3: zero transverse projection on the axis
-    L.cx = cx;
-    L.cy = cy;
+    // Eq. 3: zero transverse projection on the axis
+    const float2 cxy = __fmul2_rn(make_float2(fx, fy), make_float2(inv, inv));
+    L.cx = cxy.x;
+    L.cy = cxy.y;
     L.edr = fa.x; L.edz = fa.y;
     L.err = fa.z; L.erz = fa.w;
     L.T = fb.y;
     L.nsig = fb.y > 0.0f ? __fdividef(P.psig * fb.x, fb.y) : 0.0f;
-    L.ux = fb.z * cx; L.uy = fb.z * cy; L.uz = fb.w;
+    const float2 uxy = __fmul2_rn(make_float2(fb.z, fb.z), cxy);
+    L.ux = uxy.x; L.uy = uxy.y; L.uz = fb.w;
     L.esr = L.esz = 0.0f;
     if (P.esc4 != nullptr) {
         int pi0, pj0;
@@ -219,10 +223,17 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
                 C->cell = c;
             }
         }
-        const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
-                    v11 = pr * pz;
-        L.esr = v00 * lo.x + v10 * lo.z + v01 * hi.x + v11 * hi.z;
-        L.esz = v00 * lo.y + v10 * lo.w + v01 * hi.y + v11 * hi.w;
+        // (E_r, E_z) of the four nodes side by side: weights as above, then
+        // a product and three fused multiply-adds per component
+        const float2 vr = make_float2(1.0f - pr, pr);
+        const float2 vl = __fmul2_rn(vr, make_float2(1.0f - pz, 1.0f - pz));
+        const float2 vh = __fmul2_rn(vr, make_float2(pz, pz));
+        float2 es = __fmul2_rn(make_float2(vl.x, vl.x), make_float2(lo.x, lo.y));
+        es = __ffma2_rn(make_float2(vl.y, vl.y), make_float2(lo.z, lo.w), es);
+        es = __ffma2_rn(make_float2(vh.x, vh.x), make_float2(hi.x, hi.y), es);
+        es = __ffma2_rn(make_float2(vh.y, vh.y), make_float2(hi.z, hi.w), es);
+        L.esr = es.x;
+        L.esz = es.y;
     }
 }
 
