@@ -109,19 +109,32 @@ struct Local {
 
 // Velocity increment (a m/s per unit field) from the gathered fields: the
 // total field (Eq. 3-4) formed in (r, z) and projected once.
+// kPack (here and in the functions below): pairs of components -- (r, z),
+// (x, y) -- side by side in packed FP32x2 instructions, two results per
+// issue slot; otherwise the scalar form. The instantiation for very large
+// grids (80 registers, latency-bound on its L2 gathers) takes the scalar
+// form, which runs faster there.
+template <bool kPack = true>
 __device__ __forceinline__ void field_kick(const Local &L, float a, float dc, float srf, float &kx, float &ky,
                                            float &kz)
 {
-    // (r, z) side by side in packed FP32x2 instructions:
-    // k_rz = a ((dc E_DC + srf E_RF) + E_SCE), then (kx, ky) = k_r (cx, cy)
-    float2 t = __fmul2_rn(make_float2(dc, dc), make_float2(L.edr, L.edz));
-    t = __ffma2_rn(make_float2(srf, srf), make_float2(L.err, L.erz), t);
-    t = __fadd2_rn(t, make_float2(L.esr, L.esz));
-    t = __fmul2_rn(make_float2(a, a), t);
-    const float2 kxy = __fmul2_rn(make_float2(t.x, t.x), make_float2(L.cx, L.cy));
-    kx = kxy.x;
-    ky = kxy.y;
-    kz = t.y;
+    if constexpr (kPack) {
+        // (r, z) side by side in packed FP32x2 instructions:
+        // k_rz = a ((dc E_DC + srf E_RF) + E_SCE), then (kx, ky) = k_r (cx, cy)
+        float2 t = __fmul2_rn(make_float2(dc, dc), make_float2(L.edr, L.edz));
+        t = __ffma2_rn(make_float2(srf, srf), make_float2(L.err, L.erz), t);
+        t = __fadd2_rn(t, make_float2(L.esr, L.esz));
+        t = __fmul2_rn(make_float2(a, a), t);
+        const float2 kxy = __fmul2_rn(make_float2(t.x, t.x), make_float2(L.cx, L.cy));
+        kx = kxy.x;
+        ky = kxy.y;
+        kz = t.y;
+    } else {
+        const float kr = a * (dc * L.edr + srf * L.err + L.esr);
+        kx = kr * L.cx;
+        ky = kr * L.cy;
+        kz = a * (dc * L.edz + srf * L.erz + L.esz);
+    }
 }
 
 // Cell index and fraction along one axis; clamped to the last cell.
@@ -144,21 +157,29 @@ __device__ __forceinline__ void cell_z(int32_t zq, int n, int &j0, float &f)
 
 // Bilinear combination of four node records, each component summed in the
 // order w00 a + w10 b + w01 c + w11 d (a product, then three fused
-// multiply-adds), two components per packed FP32x2 instruction.
+// multiply-adds); kPack: two components per packed FP32x2 instruction.
+template <bool kPack = true>
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float4 c, float4 d, float w00, float w10,
                                         float w01, float w11)
 {
-    const float2 p00 = make_float2(w00, w00), p10 = make_float2(w10, w10);
-    const float2 p01 = make_float2(w01, w01), p11 = make_float2(w11, w11);
-    float2 lo = __fmul2_rn(p00, make_float2(a.x, a.y));
-    float2 hi = __fmul2_rn(p00, make_float2(a.z, a.w));
-    lo = __ffma2_rn(p10, make_float2(b.x, b.y), lo);
-    hi = __ffma2_rn(p10, make_float2(b.z, b.w), hi);
-    lo = __ffma2_rn(p01, make_float2(c.x, c.y), lo);
-    hi = __ffma2_rn(p01, make_float2(c.z, c.w), hi);
-    lo = __ffma2_rn(p11, make_float2(d.x, d.y), lo);
-    hi = __ffma2_rn(p11, make_float2(d.z, d.w), hi);
-    return make_float4(lo.x, lo.y, hi.x, hi.y);
+    if constexpr (kPack) {
+        const float2 p00 = make_float2(w00, w00), p10 = make_float2(w10, w10);
+        const float2 p01 = make_float2(w01, w01), p11 = make_float2(w11, w11);
+        float2 lo = __fmul2_rn(p00, make_float2(a.x, a.y));
+        float2 hi = __fmul2_rn(p00, make_float2(a.z, a.w));
+        lo = __ffma2_rn(p10, make_float2(b.x, b.y), lo);
+        hi = __ffma2_rn(p10, make_float2(b.z, b.w), hi);
+        lo = __ffma2_rn(p01, make_float2(c.x, c.y), lo);
+        hi = __ffma2_rn(p01, make_float2(c.z, c.w), hi);
+        lo = __ffma2_rn(p11, make_float2(d.x, d.y), lo);
+        hi = __ffma2_rn(p11, make_float2(d.z, d.w), hi);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    } else {
+        return make_float4(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x,
+                           w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y,
+                           w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z,
+                           w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w);
+    }
 }
 
 // Per-lane cache of the last PIC cell read: its index and the E_SCE of its
@@ -172,6 +193,7 @@ struct EscCache {
     float4 *lo, *hi;
 };
 
+template <bool kPack = true>
 __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float fx, float fy,
                                        float rr, int32_t zq, Local &L, EscCache *C = nullptr)
 {
@@ -184,23 +206,42 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
     const float4 a01 = __ldg(&nd[G.nr].a), a11 = __ldg(&nd[G.nr + 1].a);
     const float4 b00 = __ldg(&nd[0].b), b10 = __ldg(&nd[1].b);
     const float4 b01 = __ldg(&nd[G.nr].b), b11 = __ldg(&nd[G.nr + 1].b);
-    // weights (w00, w10) and (w01, w11): (1 - ar, ar) times 1 - az and az
-    const float2 wr = make_float2(1.0f - ar, ar);
-    const float2 wl = __fmul2_rn(wr, make_float2(1.0f - az, 1.0f - az));
-    const float2 wh = __fmul2_rn(wr, make_float2(az, az));
-    const float4 fa = lerp4(a00, a10, a01, a11, wl.x, wl.y, wh.x, wh.y);
-    const float4 fb = lerp4(b00, b10, b01, b11, wl.x, wl.y, wh.x, wh.y);
+    float w00, w10, w01, w11;
+    if constexpr (kPack) {
+        // (w00, w10) and (w01, w11): (1 - ar, ar) times 1 - az and az
+        const float2 wr = make_float2(1.0f - ar, ar);
+        const float2 wl = __fmul2_rn(wr, make_float2(1.0f - az, 1.0f - az));
+        const float2 wh = __fmul2_rn(wr, make_float2(az, az));
+        w00 = wl.x; w10 = wl.y;
+        w01 = wh.x; w11 = wh.y;
+    } else {
+        w00 = (1.0f - ar) * (1.0f - az); w10 = ar * (1.0f - az);
+        w01 = (1.0f - ar) * az; w11 = ar * az;
+    }
+    const float4 fa = lerp4<kPack>(a00, a10, a01, a11, w00, w10, w01, w11);
+    const float4 fb = lerp4<kPack>(b00, b10, b01, b11, w00, w10, w01, w11);
     const float inv = rr > 0.0f ? __fdividef(1.0f, rr) : 0.0f;
     // Eq. 3: zero transverse projection on the axis
-    const float2 cxy = __fmul2_rn(make_float2(fx, fy), make_float2(inv, inv));
-    L.cx = cxy.x;
-    L.cy = cxy.y;
+    float cx, cy;
+    if constexpr (kPack) {
+        const float2 cxy = __fmul2_rn(make_float2(fx, fy), make_float2(inv, inv));
+        cx = cxy.x; cy = cxy.y;
+    } else {
+        cx = fx * inv; cy = fy * inv;
+    }
+    L.cx = cx;
+    L.cy = cy;
     L.edr = fa.x; L.edz = fa.y;
     L.err = fa.z; L.erz = fa.w;
     L.T = fb.y;
     L.nsig = fb.y > 0.0f ? __fdividef(P.psig * fb.x, fb.y) : 0.0f;
-    const float2 uxy = __fmul2_rn(make_float2(fb.z, fb.z), cxy);
-    L.ux = uxy.x; L.uy = uxy.y; L.uz = fb.w;
+    if constexpr (kPack) {
+        const float2 uxy = __fmul2_rn(make_float2(fb.z, fb.z), make_float2(cx, cy));
+        L.ux = uxy.x; L.uy = uxy.y;
+    } else {
+        L.ux = fb.z * cx; L.uy = fb.z * cy;
+    }
+    L.uz = fb.w;
     L.esr = L.esz = 0.0f;
     if (P.esc4 != nullptr) {
         int pi0, pj0;
@@ -223,17 +264,24 @@ __device__ __forceinline__ void gather(const GridF32 &G, const InstF32 &P, float
                 C->cell = c;
             }
         }
-        // (E_r, E_z) of the four nodes side by side: weights as above, then
-        // a product and three fused multiply-adds per component
-        const float2 vr = make_float2(1.0f - pr, pr);
-        const float2 vl = __fmul2_rn(vr, make_float2(1.0f - pz, 1.0f - pz));
-        const float2 vh = __fmul2_rn(vr, make_float2(pz, pz));
-        float2 es = __fmul2_rn(make_float2(vl.x, vl.x), make_float2(lo.x, lo.y));
-        es = __ffma2_rn(make_float2(vl.y, vl.y), make_float2(lo.z, lo.w), es);
-        es = __ffma2_rn(make_float2(vh.x, vh.x), make_float2(hi.x, hi.y), es);
-        es = __ffma2_rn(make_float2(vh.y, vh.y), make_float2(hi.z, hi.w), es);
-        L.esr = es.x;
-        L.esz = es.y;
+        if constexpr (kPack) {
+            // (E_r, E_z) of the four nodes side by side: weights as above,
+            // then a product and three fused multiply-adds per component
+            const float2 vr = make_float2(1.0f - pr, pr);
+            const float2 vl = __fmul2_rn(vr, make_float2(1.0f - pz, 1.0f - pz));
+            const float2 vh = __fmul2_rn(vr, make_float2(pz, pz));
+            float2 es = __fmul2_rn(make_float2(vl.x, vl.x), make_float2(lo.x, lo.y));
+            es = __ffma2_rn(make_float2(vl.y, vl.y), make_float2(lo.z, lo.w), es);
+            es = __ffma2_rn(make_float2(vh.x, vh.x), make_float2(hi.x, hi.y), es);
+            es = __ffma2_rn(make_float2(vh.y, vh.y), make_float2(hi.z, hi.w), es);
+            L.esr = es.x;
+            L.esz = es.y;
+        } else {
+            const float v00 = (1.0f - pr) * (1.0f - pz), v10 = pr * (1.0f - pz), v01 = (1.0f - pr) * pz,
+                        v11 = pr * pz;
+            L.esr = v00 * lo.x + v10 * lo.z + v01 * hi.x + v11 * hi.z;
+            L.esz = v00 * lo.y + v10 * lo.w + v01 * hi.y + v11 * hi.w;
+        }
     }
 }
 
@@ -284,14 +332,20 @@ struct StepGas {
 // the step holds nu (dt - t) of optical depth; returns true when tau runs out
 // inside it (a candidate at t + tau / nu), else consumes that depth.
 // The relative speed w = |v - u| of the pass is returned for the candidate.
+template <bool kPack = true>
 __device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &S, float vx, float vy,
                                                float vz, float &tau, float &t, float &w)
 {
     const float cbar = 1.1283791670955126f * S.s; // 2 s / sqrt(pi)
-    const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
-    const float wz = vz - S.uz;
-    const float2 sq = __fmul2_rn(wxy, wxy);
-    w = sqrt_fast(fmaf(wz, wz, sq.x + sq.y));
+    if constexpr (kPack) {
+        const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
+        const float wz = vz - S.uz;
+        const float2 sq = __fmul2_rn(wxy, wxy);
+        w = sqrt_fast(fmaf(wz, wz, sq.x + sq.y));
+    } else {
+        const float wx = vx - S.ux, wy = vy - S.uy, wz = vz - S.uz;
+        w = sqrt_fast(wx * wx + wy * wy + wz * wz);
+    }
     const float nu = S.nsig * (w + cbar);
     const float room = nu * (P.dt - t);
     if (tau >= room) {
@@ -308,15 +362,22 @@ __device__ __forceinline__ bool next_candidate(const InstF32 &P, const StepGas &
 // scattering direction, (A.z, A.w) and (B.x, B.y) low bits the Beta uniforms,
 // (B.z, B.w) low bits the next optical depth. Returns 1 when accepted.
 // w: |v - u| from the pass of next_candidate that found the candidate.
+template <bool kPack = true>
 __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uint32_t pack, uint32_t step,
                                          uint32_t kc, float w, float &vx, float &vy, float &vz, float &eint,
                                          float &tau)
 {
+    // kPack: the x and y components of the vector arithmetic side by side in
+    // packed FP32x2 instructions (the same operations per component)
     const float s = S.s;
     const float cbar = 1.1283791670955126f * s;
-    // x and y of the vector arithmetic side by side in packed FP32x2
-    // instructions (the same operations per component)
-    const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
+    float wx, wy;
+    if constexpr (kPack) {
+        const float2 wxy = __fadd2_rn(make_float2(vx, vy), make_float2(-S.ux, -S.uy));
+        wx = wxy.x; wy = wxy.y;
+    } else {
+        wx = vx - S.ux; wy = vy - S.uy;
+    }
     const float wz = vz - S.uz;
     uint4 A = make_uint4(pack, step, 2u * kc, 0u), B = make_uint4(pack, step, 2u * kc + 1u, 0u);
     philox10x2(A, B, P.key0, P.key1);
@@ -332,26 +393,44 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     }
     const float y = -__logf(u21(A.w)) - __logf(u21(B.x)) * f;
     const float cmag = s * sqrt_fast(y);
-    float2 cxy;
-    float cz;
+    float cx, cy, cz;
     {
         const float ct = 2.0f * u21(B.y) - 1.0f;
         const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
         float sn, cs;
         sincos_2pi(u21(B.z), sn, cs);
-        const float cst = cmag * st;
-        cxy = __fmul2_rn(make_float2(cst, cst), make_float2(cs, sn));
+        if constexpr (kPack) {
+            const float cst = cmag * st;
+            const float2 cxy = __fmul2_rn(make_float2(cst, cst), make_float2(cs, sn));
+            cx = cxy.x; cy = cxy.y;
+        } else {
+            cx = cmag * st * cs;
+            cy = cmag * st * sn;
+        }
         cz = cmag * ct;
     }
-    const float2 gxy = __fadd2_rn(wxy, make_float2(-cxy.x, -cxy.y));
-    const float gz = wz - cz;
-    const float2 gg = __fmul2_rn(gxy, gxy);
-    const float g2 = fmaf(gz, gz, gg.x + gg.y);
+    float g2;
+    if constexpr (kPack) {
+        const float2 gxy = __fadd2_rn(make_float2(wx, wy), make_float2(-cx, -cy));
+        const float gz = wz - cz;
+        const float2 gg = __fmul2_rn(gxy, gxy);
+        g2 = fmaf(gz, gz, gg.x + gg.y);
+    } else {
+        const float gx = wx - cx, gy = wy - cy, gz = wz - cz;
+        g2 = gx * gx + gy * gy + gz * gz;
+    }
     const float g = sqrt_fast(g2);
     if (!(u21(A.y) * (w + cmag) < g)) return 0;
-    const float2 Vxy = __ffma2_rn(make_float2(P.fM, P.fM), make_float2(vx, vy),
-                                  __fmul2_rn(make_float2(P.fm, P.fm),
-                                             __fadd2_rn(make_float2(S.ux, S.uy), cxy)));
+    float Vx, Vy;
+    if constexpr (kPack) {
+        const float2 Vxy = __ffma2_rn(make_float2(P.fM, P.fM), make_float2(vx, vy),
+                                      __fmul2_rn(make_float2(P.fm, P.fm),
+                                                 __fadd2_rn(make_float2(S.ux, S.uy), make_float2(cx, cy))));
+        Vx = Vxy.x; Vy = Vxy.y;
+    } else {
+        Vx = P.fM * vx + P.fm * (S.ux + cx);
+        Vy = P.fM * vy + P.fm * (S.uy + cy);
+    }
     const float Vz = P.fM * vz + P.fm * (S.uz + cz);
     const float etr = P.mu_2kb * g2;
     const float ec = etr + eint;
@@ -367,10 +446,14 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     const float st = sqrt_fast(fmaxf(0.0f, 1.0f - ct * ct));
     float sn, cs;
     sincos_2pi(u22(A.x, A.y), sn, cs);
-    const float gst = gn * st;
-    const float2 nv = __ffma2_rn(make_float2(gst, gst), make_float2(cs, sn), Vxy);
-    vx = nv.x;
-    vy = nv.y;
+    if constexpr (kPack) {
+        const float gst = gn * st;
+        const float2 nv = __ffma2_rn(make_float2(gst, gst), make_float2(cs, sn), make_float2(Vx, Vy));
+        vx = nv.x; vy = nv.y;
+    } else {
+        vx = Vx + gn * st * cs;
+        vy = Vy + gn * st * sn;
+    }
     vz = Vz + gn * ct;
     return 1;
 }
@@ -450,6 +533,7 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
 // Velocity increment kick * E_tot over one step at the RK4 stage position
 // x + h v (h v given in m/s times the step, i.e. the stage's fraction of
 // the step times the stage velocity), with RF scalar srf.
+template <bool kPack = true>
 __device__ __forceinline__ void stage_kick(const GridF32 &G, const InstF32 &P, int32_t xq, int32_t yq,
                                            int32_t zq, float hvx, float hvy, float hvz, float srf, float &kx,
                                            float &ky, float &kz)
@@ -459,8 +543,8 @@ __device__ __forceinline__ void stage_kick(const GridF32 &G, const InstF32 &P, i
     const int32_t sz = zq + __float2int_rn(fminf(fmaxf(hvz * P.czs, -1.0e9f), 1.0e9f));
     const float fx = (float)sx, fy = (float)sy;
     Local L;
-    gather(G, P, fx, fy, lattice_r(fx, fy), sz, L);
-    field_kick(L, P.kick, P.dc_scale, srf, kx, ky, kz);
+    gather<kPack>(G, P, fx, fy, lattice_r(fx, fy), sz, L);
+    field_kick<kPack>(L, P.kick, P.dc_scale, srf, kx, ky, kz);
 }
 
 // Counters of a warp added to the instance's totals.
@@ -494,7 +578,7 @@ __device__ __forceinline__ void deposit_at_end(const InstF32 &P, int32_t xq, int
 
 // Kick and drift of step n with kick (kx, ky, kz) evaluated at x_n (RK4:
 // the first stage), then the lattice radius and class at x_{n+1}.
-template <bool kExtras>
+template <bool kExtras, bool kPack = true>
 __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
                                     uint32_t h1, uint32_t h2, float kx, float ky, float kz, int32_t &xq,
                                     int32_t &yq, int32_t &zq, float &vx, float &vy, float &vz, float &fx,
@@ -505,11 +589,11 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
         // and t + dt; stage positions rounded to the lattice
         const float sh = s_rf[2 * k + 1], s1 = s_rf[2 * k + 2];
         float k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
-        stage_kick(G, P, xq, yq, zq, 0.5f * vx, 0.5f * vy, 0.5f * vz, sh, k2x, k2y, k2z);
+        stage_kick<kPack>(G, P, xq, yq, zq, 0.5f * vx, 0.5f * vy, 0.5f * vz, sh, k2x, k2y, k2z);
         const float v2x = vx + 0.5f * kx, v2y = vy + 0.5f * ky, v2z = vz + 0.5f * kz;
-        stage_kick(G, P, xq, yq, zq, 0.5f * v2x, 0.5f * v2y, 0.5f * v2z, sh, k3x, k3y, k3z);
+        stage_kick<kPack>(G, P, xq, yq, zq, 0.5f * v2x, 0.5f * v2y, 0.5f * v2z, sh, k3x, k3y, k3z);
         const float v3x = vx + 0.5f * k2x, v3y = vy + 0.5f * k2y, v3z = vz + 0.5f * k2z;
-        stage_kick(G, P, xq, yq, zq, v3x, v3y, v3z, s1, k4x, k4y, k4z);
+        stage_kick<kPack>(G, P, xq, yq, zq, v3x, v3y, v3z, s1, k4x, k4y, k4z);
         const float v4x = vx + k3x, v4y = vy + k3y, v4z = vz + k3z;
         const float c6 = 1.0f / 6.0f;
         const float ux = (vx + 2.0f * v2x + 2.0f * v3x + v4x) * c6;
@@ -521,7 +605,7 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
         xq += lattice_step(ux * P.cxs, dither(h2, 0));
         yq += lattice_step(uy * P.cxs, dither(h2, 11));
         zq += lattice_step(uz * P.czs, dither(h2, 22));
-    } else {
+    } else if (kPack) {
         // x and y side by side in packed FP32x2 instructions (the same
         // operations per component as add_sr and lattice_step)
         const float2 v = make_float2(vx, vy), d = make_float2(kx, ky);
@@ -537,6 +621,13 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
         xq += lattice_step(sxy.x, dither(h2, 0));
         yq += lattice_step(sxy.y, dither(h2, 11));
         zq += lattice_step(vz * P.czs, dither(h2, 22));
+    } else {
+        vx = add_sr(vx, kx, dither_c(h1, 0));
+        vy = add_sr(vy, ky, dither_c(h1, 11));
+        vz = add_sr(vz, kz, dither_c(h1, 22));
+        xq += lattice_step(vx * P.cxs, dither(h2, 0));
+        yq += lattice_step(vy * P.cxs, dither(h2, 11));
+        zq += lattice_step(vz * P.czs, dither(h2, 22));
     }
     fx = (float)xq;
     fy = (float)yq;
@@ -545,10 +636,11 @@ __device__ __forceinline__ int push(const GridF32 &G, const InstF32 &P, const fl
 }
 
 // Kick of step k at the gathered fields.
+template <bool kPack = true>
 __device__ __forceinline__ void kick_of(const InstF32 &P, const Local &L, float srf, float &kx, float &ky,
                                         float &kz)
 {
-    field_kick(L, P.kick, P.dc_scale, srf, kx, ky, kz);
+    field_kick<kPack>(L, P.kick, P.dc_scale, srf, kx, ky, kz);
 }
 
 // Collision-free tile: the U x blockDim.x packs of instance P starting at
@@ -638,15 +730,15 @@ __device__ __forceinline__ void run_tile_free(const GridF32 &G, const InstF32 &P
 // Start of step k of one pack: gather at x_k, the step's kick, the Langevin
 // switch, and the first pass of the candidate loop. Returns whether a
 // collision candidate is pending.
-template <bool kExtras>
+template <bool kExtras, bool kPack = true>
 __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, const float *s_rf, int k,
                                            uint32_t pack, float fx, float fy, float rr, int32_t zq,
                                            float &vx, float &vy, float &vz, float &tau, float &t,
                                            float &w, bool &lv, StepGas &S, EscCache &C)
 {
     Local L;
-    gather(G, P, fx, fy, rr, zq, L, &C);
-    kick_of(P, L, s_rf[2 * k], S.kx, S.ky, S.kz);
+    gather<kPack>(G, P, fx, fy, rr, zq, L, &C);
+    kick_of<kPack>(P, L, s_rf[2 * k], S.kx, S.ky, S.kz);
     S.nsig = L.nsig; S.T = L.T;
     S.ux = L.ux; S.uy = L.uy; S.uz = L.uz;
     t = 0.0f;
@@ -659,7 +751,7 @@ __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, c
         langevin_step(P, S, pack, (uint32_t)(P.step0 + k), vx, vy, vz);
         return false;
     }
-    return next_candidate(P, S, vx, vy, vz, tau, t, w);
+    return next_candidate<kPack>(P, S, vx, vy, vz, tau, t, w);
 }
 
 // Tile with collisions. Each lane owns a pack and walks through its steps;
@@ -671,7 +763,7 @@ __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, c
 // has none, whichever serves more lanes. Lanes drift apart in step index;
 // every pack still takes exactly its own sequence of operations, so results
 // do not depend on the schedule.
-template <bool kExtras>
+template <bool kExtras, bool kPack>
 __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P, const float *s_rf,
                                               int64_t off, int nsteps, float4 *s_esc)
 {
@@ -700,7 +792,8 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         C.lo = s_esc + threadIdx.x;
         C.hi = s_esc + blockDim.x + threadIdx.x;
     }
-    if (live) pend = begin_step<kExtras>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S, C);
+    if (live)
+        pend = begin_step<kExtras, kPack>(G, P, s_rf, 0, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S, C);
     for (;;) {
         const bool can_push = live && !pend;
         const unsigned mc = __ballot_sync(0xffffffffu, pend);
@@ -708,13 +801,13 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         if ((mc | mp) == 0u) break;
         if (mc != 0u && __popc(mc) >= __popc(mp)) {
             if (pend) {
-                n_coll += (unsigned)candidate(P, S, pack, (uint32_t)(P.step0 + k), (uint32_t)kc, w, vx, vy,
+                n_coll += (unsigned)candidate<kPack>(P, S, pack, (uint32_t)(P.step0 + k), (uint32_t)kc, w, vx, vy,
                                               vz, eint, tau);
                 if (++kc == kKmax) {
                     ++n_ovf; // candidate cap: the rest of the step holds no further candidate
                     pend = false;
                 } else {
-                    pend = next_candidate(P, S, vx, vy, vz, tau, t, w);
+                    pend = next_candidate<kPack>(P, S, vx, vy, vz, tau, t, w);
                 }
             }
         } else if (can_push) {
@@ -726,13 +819,15 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
                 const float kdt = P.tst_a_dt * Te * __expf(-P.tst_b * __frcp_rn(Te));
                 lnsy = add_sr(lnsy, -kdt, dither_c(fmix32(h1 ^ 0x68E31DA4u), 0));
             }
-            st = push<kExtras>(G, P, s_rf, k, h1, h2, S.kx, S.ky, S.kz, xq, yq, zq, vx, vy, vz, fx, fy, rr);
+            st = push<kExtras, kPack>(G, P, s_rf, k, h1, h2, S.kx, S.ky, S.kz, xq, yq, zq, vx, vy, vz, fx, fy,
+                                      rr);
             ++k;
             kc = 0;
             if (st != MUCITE_ACTIVE || k == nsteps)
                 live = false;
             else
-                pend = begin_step<kExtras>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv, S, C);
+                pend = begin_step<kExtras, kPack>(G, P, s_rf, k, pack, fx, fy, rr, zq, vx, vy, vz, tau, t, w, lv,
+                                                  S, C);
         }
     }
     if (owned) {
@@ -897,7 +992,7 @@ __global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
         constexpr int kU = kCollide ? 1 : kFreeU;
         const int64_t off = (int64_t)(t - __ldg(&tile_start[lo])) * (kU * blockDim.x);
         if (kCollide)
-            run_tile_coll<kExtras>(G, P, s_rf, off, nsteps, s_esc);
+            run_tile_coll<kExtras, kMinBlocks != 3>(G, P, s_rf, off, nsteps, s_esc);
         else
             run_tile_free<kExtras, kU>(G, P, s_rf, off, nsteps);
     }
