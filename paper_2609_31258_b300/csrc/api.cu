@@ -322,6 +322,8 @@ void bind_params(mucite_ctx *ctx, Instance &I)
         P.ecap = std::isinf(pf.ecap) ? 3.0e38f : (float)pf.ecap;
         P.key0 = (uint32_t)r.seed;
         P.key1 = (uint32_t)(r.seed >> 32);
+        for (int k = 0; k < 10; ++k)
+            P.rkey[k] = make_uint2(P.key0 + (uint32_t)k * 0x9E3779B9u, P.key1 + (uint32_t)k * 0xBB67AE85u);
         P.zexit_q = zexit_q;
         P.rdet2 = (uint64_t)(rdet_q * rdet_q);
         P.hit = (float)r.hit_dist;

@@ -46,6 +46,28 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// One block with precomputed round keys.
+__device__ __forceinline__ uint4 philox10(uint4 c, const uint2 *rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint2 k = rk[round];
+        philox_round(c, k.x, k.y);
+    }
+    return c;
+}
+
+// Two blocks with precomputed round keys, rounds interleaved.
+__device__ __forceinline__ void philox10x2(uint4 &a, uint4 &b, const uint2 *rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint2 k = rk[round];
+        philox_round(a, k.x, k.y);
+        philox_round(b, k.x, k.y);
+    }
+}
+
 // Two blocks under the same key, rounds interleaved (one key schedule).
 __device__ __forceinline__ void philox10x2(uint4 &a, uint4 &b, uint32_t k0, uint32_t k1)
 {
@@ -130,6 +152,9 @@ struct InstF32 {
     float lv_c;                // gamma = lv_c * (n sigma) * sqrt(T)
     float lv_kM;               // k_B / M
     uint32_t key0, key1;
+    uint2 rkey[10];            // Philox round keys (key0 + r W0, key1 + r W1), r = 0..9, formed on
+                               // the host once: the kernels read them instead of advancing the key
+                               // between rounds
     int64_t zexit_q;           // first lattice z counted as crossed
     uint64_t rdet2;            // (floor(r_det / R * 2^30))^2
     float hit;                 // electrode-hit distance [m]

@@ -380,7 +380,7 @@ __device__ __forceinline__ int candidate(const InstF32 &P, const StepGas &S, uin
     }
     const float wz = vz - S.uz;
     uint4 A = make_uint4(pack, step, 2u * kc, 0u), B = make_uint4(pack, step, 2u * kc + 1u, 0u);
-    philox10x2(A, B, P.key0, P.key1);
+    philox10x2(A, B, P.rkey);
     tau = -__logf(u22(B.z, B.w));
     // Partner |c'|^2 / s^2 ~ Gamma(k, 1), isotropic: k = 3/2 (Maxwellian)
     // or 2 (speed-weighted); Gamma(3/2) = Exp(1) + N^2/2 with
@@ -482,7 +482,7 @@ __device__ __forceinline__ void langevin_step(const InstF32 &P, const StepGas &L
     const float gdt = P.lv_c * L.nsig * sqT * P.dt;
     const float decay = __expf(-gdt);
     const float sd = sqT * sqrt_fast(P.lv_kM * -expm1f(-2.0f * gdt));
-    const uint4 U = philox10(make_uint4(pack, step, 128u, 0u), P.key0, P.key1);
+    const uint4 U = philox10(make_uint4(pack, step, 128u, 0u), P.rkey);
     const float r01 = sd * sqrt_fast(-2.0f * __logf(u01f(U.x)));
     const float r23 = sd * sqrt_fast(-2.0f * __logf(u01f(U.z)));
     float sn, cs, sn2, cs2;
