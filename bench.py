@@ -733,6 +733,9 @@ def main():
                 "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
                 "inst_per_pack_step": insts, "pack_steps_per_launch": ps_per_launch,
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
+                "issue_active": None if stale else prof.get("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+                "note": "executed thread instructions over issue slots: fewer instructions per pack-step at the "
+                        "same issue activity lower this fraction while raising the pack-step rate",
                 "hbm_bytes_per_pack_step_at_launch": 65.0 / (args.spl or 2000)}
 
     if args.section == "fused":
