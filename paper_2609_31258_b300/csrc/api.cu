@@ -53,6 +53,12 @@ struct mucite_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr; // captures the bodies of device-controlled solve loops
+    // streams the per-instance collision launches of a batch run side by side
+    // on (forked from and joined back into the context stream by events)
+    static constexpr int kStepStreams = 8;
+    cudaStream_t step_streams[kStepStreams] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kStepStreams] = {};
     bool device_loops = true;   // cleared if a driver cannot build them: fixed pass sequences instead
     std::string err;
     bool fields = false;
@@ -98,6 +104,8 @@ struct mucite_ctx {
     int64_t launches = 0;
     int64_t graph_replays = 0, graph_captures = 0;
     InstF32 inst0{};             // host copy of the first descriptor of the last step upload
+    std::vector<InstF32> h_insts;   // host copies of the descriptors of the last step upload
+    std::vector<int32_t> h_tiles;   // and of its tile starts
     // captured macro step of the last group (replayed while the group is unchanged)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
@@ -657,6 +665,8 @@ mucite_status step_upload(mucite_ctx *ctx, const std::vector<Instance *> &grp, i
                        ctx->stream));
     ctx->inst0 = host[0]; // the descriptor a single-instance launch takes as a kernel parameter
     ctx->inst0.hold_tile = -1;
+    ctx->h_insts = host;  // the descriptors collision launches take as kernel parameters
+    ctx->h_tiles = tiles;
     return MUCITE_OK;
 }
 
@@ -706,8 +716,34 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
         const int per_sm = std::min(pers, std::max(1, step_f32_blocks_per_sm(grid_f32(ctx), ctx->threads, chunk, collide, extras, pic)));
         grid = std::min(total_tiles, per_sm * ctx->sm_count);
     }
-    launch_step_f32(grid_f32(ctx), ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads,
-                    chunk, grid, collide, extras, pic, ctx->stream);
+    const GridF32 G = grid_f32(ctx);
+    if (collide && !step_f32_large_grid(G)) {
+        // one launch per instance, each with its descriptor as the kernel
+        // parameter; a batch's launches forked onto the step streams
+        const int n = (int)grp.size();
+        launch_rf_table(ctx->d_insts, n, chunk, ctx->stream);
+        auto one = [&](int k, cudaStream_t st) {
+            const int tiles = ctx->h_tiles[k + 1] - ctx->h_tiles[k];
+            const int g = grid >= total_tiles ? tiles : std::min(grid, tiles);
+            launch_step_f32_one(G, ctx->h_insts[k], ctx->d_insts + k, tiles, ctx->threads, chunk, g, extras, pic,
+                                st);
+        };
+        if (n == 1) {
+            one(0, ctx->stream);
+            return 2;
+        }
+        const int ns = std::min(n, mucite_ctx::kStepStreams);
+        cudaEventRecord(ctx->ev_fork, ctx->stream);
+        for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(ctx->step_streams[i], ctx->ev_fork, 0);
+        for (int k = 0; k < n; ++k) one(k, ctx->step_streams[k % ns]);
+        for (int i = 0; i < ns; ++i) {
+            cudaEventRecord(ctx->ev_join[i], ctx->step_streams[i]);
+            cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0);
+        }
+        return 1 + n;
+    }
+    launch_step_f32(G, ctx->d_insts, ctx->d_tiles, (int)grp.size(), total_tiles, ctx->threads, chunk, grid,
+                    collide, extras, pic, ctx->stream);
     return 2;
 }
 
@@ -756,13 +792,16 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
             st = step_upload(ctx, grp, chunk, tiles, fused);
             if (st != MUCITE_OK) return st;
             {
-                // a kernel may take the first descriptor by value: any change
-                // of it other than the clock needs a new capture
-                InstF32 d = ctx->inst0;
-                d.step0 = 0;
+                // the kernels take descriptors by value: any change of them
+                // other than the clock needs a new capture
                 uint64_t h = 1469598103934665603ull; // FNV-1a
-                const unsigned char *b = reinterpret_cast<const unsigned char *>(&d);
-                for (size_t k = 0; k < sizeof d; ++k) h = (h ^ b[k]) * 1099511628211ull;
+                std::vector<InstF32> all = ctx->h_insts;
+                all.push_back(ctx->inst0);
+                for (InstF32 d : all) {
+                    d.step0 = 0;
+                    const unsigned char *b = reinterpret_cast<const unsigned char *>(&d);
+                    for (size_t k = 0; k < sizeof d; ++k) h = (h ^ b[k]) * 1099511628211ull;
+                }
                 key.push_back((const void *)(uintptr_t)h);
             }
             if (P0 > 0) {
@@ -875,6 +914,15 @@ mucite_status step_f64_one(mucite_ctx *ctx, Instance &I, int64_t nsteps)
 
 extern "C" {
 
+static void destroy_step_streams(mucite_ctx *ctx)
+{
+    for (int i = 0; i < mucite_ctx::kStepStreams; ++i) {
+        if (ctx->step_streams[i]) cudaStreamDestroy(ctx->step_streams[i]);
+        if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+}
+
 mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
 {
     if (!out) return fail(nullptr, MUCITE_E_ARG, "out is NULL");
@@ -901,6 +949,11 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMemset(ctx->d_tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    for (int i = 0; i < mucite_ctx::kStepStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&ctx->step_streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fail(nullptr, MUCITE_E_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
         dfree(ctx->d_insts);
@@ -913,6 +966,7 @@ mucite_status mucite_create(mucite_ctx **out, int device, void *cuda_stream)
         dfree(ctx->d_tc_err);
         dfree(ctx->d_tc_maps);
         if (ctx->aux) cudaStreamDestroy(ctx->aux);
+        destroy_step_streams(ctx);
         delete ctx;
         return MUCITE_E_OOM;
     }
@@ -940,6 +994,7 @@ void mucite_destroy(mucite_ctx *ctx)
     dfree(ctx->d_limits);
     drop_graph(ctx);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    destroy_step_streams(ctx);
     delete ctx;
 }
 

@@ -43,6 +43,17 @@ void launch_step_f32(const GridF32 &G, InstF32 *d_insts, const int32_t *d_tile_s
                      int total_tiles, int threads, int nsteps, int grid, bool collide, bool extras,
                      bool esc_cache, cudaStream_t s);
 void launch_advance_clock(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
+// Grids above 64 MB of node records (their collision launches keep the
+// batched kernel with its scalar arithmetic).
+bool step_f32_large_grid(const GridF32 &G);
+// RF scalars of the next nsteps micro steps of every instance (P.rf).
+void launch_rf_table(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
+// Collision launch of one instance on a grid of at most 64 MB: h_inst (the
+// host copy of the descriptor uploaded to d_inst) is the kernel parameter;
+// tiles of threads packs; grid < total_tiles strides over them. The RF
+// scalars come from launch_rf_table.
+void launch_step_f32_one(const GridF32 &G, const InstF32 &h_inst, const InstF32 *d_inst, int total_tiles,
+                         int threads, int nsteps, int grid, bool extras, bool esc_cache, cudaStream_t s);
 int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras,
                            bool esc_cache);
 // One collision-free micro step of one instance (no Eq. 7, Langevin or RK4)
