@@ -730,7 +730,7 @@ def main():
     ach = insts * ps_per_launch / (kern_ms * 1e-3) / 1e9 if insts else None
     roofline = {"bound": "alu", "achieved": ach, "peak": peak_ginst, "unit": "Ginst/s (thread instructions)",
                 "frac": (ach / peak_ginst) if ach else None, "traffic": traffic, "profile_stale": stale,
-                "kernel": "step_f32_kernel", "kernel_ms_per_launch": kern_ms,
+                "kernel": "step_f32_one_kernel", "kernel_ms_per_launch": kern_ms,
                 "inst_per_pack_step": insts, "pack_steps_per_launch": ps_per_launch,
                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock (issue-bound ALU peak)",
                 "issue_active": None if stale else prof.get("smsp__issue_active.avg.pct_of_peak_sustained_active"),
@@ -978,7 +978,8 @@ def _sweep(args, local, stream, dev):
     return {"value": ps / (ms * 1e-3), "unit": UNIT, "instances": len(pts),
             "packs": int(sum(pt["n_packs"] for pt in pts)), "micro_steps": K, "ms": ms,
             "pic": "128x512 per instance, every 10 micro steps", "tuning": tuning,
-            "note": "macro step = batched PIC update of all instances + one fused launch of 10 micro steps, "
+            "note": "macro step = batched PIC update of all instances + one launch of 10 micro steps per instance "
+                    "(side by side on the context's step streams), "
                     "graph-replayed"}
 
 
