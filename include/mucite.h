@@ -322,10 +322,13 @@ mucite_status mucite_set_dt(mucite_ctx *ctx, int instance, double dt);
 mucite_status mucite_dt_limits(mucite_ctx *ctx, int instance, double out[6]);
 
 /* Launch mode of the batched FP32 step (the paper runs independent cases as
- * separate processes, Supporting Information S6; here many instances share
- * one launch). persistent_blocks_per_sm > 0: a persistent launch of that many
- * blocks per SM (capped by occupancy) whose blocks stride over the tiles of
- * every instance (block b takes tiles b, b + grid, ...); 0: automatic, the
+ * separate processes, Supporting Information S6; here many instances are
+ * stepped together: collision-free steps in one launch over all instances,
+ * steps with collisions on grids up to 64 MB in one launch per instance, the
+ * launches of a batch side by side on the context's step streams, larger
+ * grids in one launch). persistent_blocks_per_sm > 0: persistent launches of
+ * that many blocks per SM (capped by occupancy) whose blocks stride over the
+ * tiles of their instances (block b takes tiles b, b + grid, ...); 0: automatic, the
  * occupancy-sized persistent grid for collision-free launches of at most 16
  * micro steps, one block per tile otherwise.
  * use_graphs != 0: when all stepped instances share the space-charge
