@@ -55,7 +55,7 @@ struct mucite_ctx {
     cudaStream_t aux = nullptr; // captures the bodies of device-controlled solve loops
     // streams the per-instance collision launches of a batch run side by side
     // on (forked from and joined back into the context stream by events)
-    static constexpr int kStepStreams = 8;
+    static constexpr int kStepStreams = 16;
     cudaStream_t step_streams[kStepStreams] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kStepStreams] = {};
