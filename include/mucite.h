@@ -251,6 +251,7 @@ typedef struct {
     int32_t steps_per_launch;         /* micro steps fused per launch (PIC runs: unchanged) */
     int32_t threads_per_block;        /* packs per tile, as in mucite_set_tuning */
     int32_t persistent_blocks_per_sm; /* as in mucite_set_launch_mode (0 = automatic) */
+    int32_t schedule;                 /* collision-loop schedule, as in mucite_set_schedule */
     int32_t n_tried;                  /* shapes timed */
     double best_ms_per_step;          /* device time of one micro step of the set, chosen shape */
 } mucite_tuning;
@@ -260,7 +261,8 @@ typedef struct {
  * injected FP32 instance, listed once) for every candidate shape -- packs
  * per tile {64, 128, 256} x persistent blocks per SM {0, 1, 2, 3} x steps
  * per launch {250, 500, 1000, 2000} up to trial_steps / 2 (with space
- * charge on, the PIC interval fixes the steps per launch) -- each from the
+ * charge on, the PIC interval fixes the steps per launch, and both
+ * schedules of mucite_set_schedule are tried as well) -- each from the
  * same saved state after an untimed pass of the same shape, then restores
  * that state (pools, clocks, slot counts, source accumulators, counters,
  * PIC charge, potential and field) and applies the fastest shape to the
@@ -358,6 +360,22 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
 #define MUCITE_DST_SIMT 0
 #define MUCITE_DST_TENSOR_CORES 1
 mucite_status mucite_set_pic_solver(mucite_ctx *ctx, int contraction);
+
+/* Schedule of the collision loop in the per-instance collision launches (no
+ * counterpart in the paper; results do not depend on it). A lane of a warp
+ * owns a pack, and each iteration of the warp either tries one pending
+ * collision candidate of every lane that has one or finishes the micro step
+ * of every lane that has none. MUCITE_SCHEDULE_BALANCED (default) takes
+ * whichever serves more lanes, the better choice where candidates are common
+ * and launches are long; MUCITE_SCHEDULE_EAGER takes the candidates as soon
+ * as their lanes number at least a sixth of those ready to step, so that in
+ * launches of a few micro steps (the steps between space-charge updates)
+ * with rare candidates no lane falls steps behind and finishes the launch
+ * nearly alone. mucite_autotune tries both when space charge fixes the
+ * steps per launch. Errors: MUCITE_E_ARG (unknown schedule). */
+#define MUCITE_SCHEDULE_BALANCED 1
+#define MUCITE_SCHEDULE_EAGER 6
+mucite_status mucite_set_schedule(mucite_ctx *ctx, int schedule);
 
 /* Test hook (no counterpart in the paper; for tests of the failure path,
  * never for production runs). MUCITE_HOOK_HOLD_STAGED_COPY with value v >= 0:

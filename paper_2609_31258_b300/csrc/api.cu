@@ -49,6 +49,8 @@ struct Instance {
 
 } // namespace
 
+static_assert(MUCITE_SCHEDULE_EAGER == kEagerWeight, "the eager schedule is the eager kernel instantiation");
+
 struct mucite_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -100,6 +102,7 @@ struct mucite_ctx {
     int steps_per_launch = 256;
     int threads = 256;
     int persistent = 0;          // blocks per SM of a persistent launch, 0 = one block per tile
+    int schedule = MUCITE_SCHEDULE_BALANCED; // candidate weight of the collision loop (kEagerWeight: eager)
     int use_graphs = 1;
     int64_t launches = 0;
     int64_t graph_replays = 0, graph_captures = 0;
@@ -726,7 +729,7 @@ int64_t step_launch(mucite_ctx *ctx, const std::vector<Instance *> &grp, int tot
             const int tiles = ctx->h_tiles[k + 1] - ctx->h_tiles[k];
             const int g = grid >= total_tiles ? tiles : std::min(grid, tiles);
             launch_step_f32_one(G, ctx->h_insts[k], ctx->d_insts + k, tiles, ctx->threads, chunk, g, extras, pic,
-                                st);
+                                ctx->schedule, st);
         };
         if (n == 1) {
             one(0, ctx->stream);
@@ -778,6 +781,7 @@ mucite_status step_f32_group(mucite_ctx *ctx, std::vector<Instance *> &grp, int6
             key.push_back((const void *)(intptr_t)unroll);
             key.push_back((const void *)(intptr_t)ctx->threads);
             key.push_back((const void *)(intptr_t)ctx->persistent);
+            key.push_back((const void *)(intptr_t)ctx->schedule);
             for (Instance *I : grp) {
                 key.push_back(I);
                 key.push_back((const void *)(intptr_t)I->n_slots);
@@ -1541,18 +1545,24 @@ mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, 
     }
     const int threads_c[] = {64, 128, 256};
     const int pers_c[] = {0, 1, 2, 3};
+    // launches as short as the PIC interval: both collision-loop schedules
+    std::vector<int> scheds{MUCITE_SCHEDULE_BALANCED};
+    if (pic) scheds.push_back(MUCITE_SCHEDULE_EAGER);
     const int save_spl = ctx->steps_per_launch, save_thr = ctx->threads, save_pers = ctx->persistent;
+    const int save_sched = ctx->schedule;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = -1.0;
-    int bspl = save_spl, bthr = save_thr, bpers = save_pers, tried = 0;
+    int bspl = save_spl, bthr = save_thr, bpers = save_pers, bsched = save_sched, tried = 0;
     for (int spl : spls)
+        for (int sched : scheds)
         for (int thr : threads_c)
             for (int pers : pers_c) {
                 ctx->steps_per_launch = spl;
                 ctx->threads = thr;
                 ctx->persistent = pers;
+                ctx->schedule = sched;
                 drop_graph(ctx);
                 // untimed pass of the same shape (graph capture, caches), then the timed one
                 for (int pass = 0; pass < 2 && st == MUCITE_OK; ++pass) {
@@ -1572,6 +1582,7 @@ mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, 
                     bspl = spl;
                     bthr = thr;
                     bpers = pers;
+                    bsched = sched;
                 }
             }
     cudaEventDestroy(e0);
@@ -1583,14 +1594,17 @@ mucite_status mucite_autotune(mucite_ctx *ctx, const int *instances, int count, 
         ctx->steps_per_launch = save_spl;
         ctx->threads = save_thr;
         ctx->persistent = save_pers;
+        ctx->schedule = save_sched;
         return st != MUCITE_OK ? st : rs;
     }
     ctx->steps_per_launch = bspl;
     ctx->threads = bthr;
     ctx->persistent = bpers;
+    ctx->schedule = bsched;
     out->steps_per_launch = bspl;
     out->threads_per_block = bthr;
     out->persistent_blocks_per_sm = bpers;
+    out->schedule = bsched;
     out->n_tried = tried;
     out->best_ms_per_step = best / trial_steps;
     return MUCITE_OK;
@@ -1826,6 +1840,17 @@ mucite_status mucite_set_launch_mode(mucite_ctx *ctx, int persistent_blocks_per_
     drop_graph(ctx);
     ctx->persistent = persistent_blocks_per_sm;
     ctx->use_graphs = use_graphs ? 1 : 0;
+    return MUCITE_OK;
+}
+
+mucite_status mucite_set_schedule(mucite_ctx *ctx, int schedule)
+{
+    if (!ctx) return MUCITE_E_ARG;
+    if (schedule != MUCITE_SCHEDULE_BALANCED && schedule != MUCITE_SCHEDULE_EAGER)
+        return fail(ctx, MUCITE_E_ARG, "unknown collision-loop schedule %d", schedule);
+    DevGuard dg(ctx->device);
+    if (schedule != ctx->schedule) drop_graph(ctx);
+    ctx->schedule = schedule;
     return MUCITE_OK;
 }
 

@@ -18,6 +18,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kPlanck = 6.62607015e-34;           // Planck constant [J s]
 constexpr double kR = 1.380649e-23 * 6.02214076e23;  // molar gas constant k_B N_A [J/(mol K)]
 constexpr int kCounters = 4;            // per-instance device counters (InstF32::counters)
+constexpr int kEagerWeight = 6;         // candidate weight of the eager collision schedule
 constexpr double kLat = 1073741824.0;      // 2^30 lattice units per R (r) or per (z1 - z0) (z)
 constexpr int kKmax = 32;                  // collision candidates examined per pack per step
 

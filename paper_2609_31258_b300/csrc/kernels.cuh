@@ -51,9 +51,11 @@ void launch_rf_table(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s);
 // Collision launch of one instance on a grid of at most 64 MB: h_inst (the
 // host copy of the descriptor uploaded to d_inst) is the kernel parameter;
 // tiles of threads packs; grid < total_tiles strides over them. The RF
-// scalars come from launch_rf_table.
+// scalars come from launch_rf_table. cand_weight: the candidate weight of the
+// collision loop's schedule, 1 or kEagerWeight (results do not depend on it).
 void launch_step_f32_one(const GridF32 &G, const InstF32 &h_inst, const InstF32 *d_inst, int total_tiles,
-                         int threads, int nsteps, int grid, bool extras, bool esc_cache, cudaStream_t s);
+                         int threads, int nsteps, int grid, bool extras, bool esc_cache, int cand_weight,
+                         cudaStream_t s);
 int step_f32_blocks_per_sm(const GridF32 &G, int threads, int nsteps, bool collide, bool extras,
                            bool esc_cache);
 // One collision-free micro step of one instance (no Eq. 7, Langevin or RK4)

@@ -762,8 +762,12 @@ __device__ __forceinline__ bool begin_step(const GridF32 &G, const InstF32 &P, c
 // finishes the step (kick, drift, classify, next gather) of each lane that
 // has none, whichever serves more lanes. Lanes drift apart in step index;
 // every pack still takes exactly its own sequence of operations, so results
-// do not depend on the schedule.
-template <bool kExtras, bool kPack>
+// do not depend on the schedule. kW > 1 serves the pending candidates as
+// soon as their lanes are at least 1 / kW of those ready to push: in
+// launches of a few micro steps, where candidates are rare, lanes that wait
+// for enough others to have a candidate fall steps behind, and the launch
+// ends with them running nearly alone.
+template <bool kExtras, bool kPack, int kW = 1>
 __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P, const float *s_rf,
                                               int64_t off, int nsteps, float4 *s_esc, int64_t step0)
 {
@@ -799,7 +803,7 @@ __device__ __forceinline__ void run_tile_coll(const GridF32 &G, const InstF32 &P
         const unsigned mc = __ballot_sync(0xffffffffu, pend);
         const unsigned mp = __ballot_sync(0xffffffffu, can_push);
         if ((mc | mp) == 0u) break;
-        if (mc != 0u && __popc(mc) >= __popc(mp)) {
+        if (mc != 0u && kW * __popc(mc) >= __popc(mp)) {
             if (pend) {
                 n_coll += (unsigned)candidate<kPack>(P, S, pack, (uint32_t)(step0 + k), (uint32_t)kc, w, vx, vy,
                                               vz, eint, tau);
@@ -1007,7 +1011,7 @@ __global__ void __launch_bounds__(kCollide ? 256 : 128, kMinBlocks)
 // step streams), so an instance gives the same results alone and in any
 // batch. Only the step clock, advanced on the device between graph replays,
 // is read from the descriptor array.
-template <bool kExtras>
+template <bool kExtras, int kW>
 __global__ void __launch_bounds__(256, 4)
     step_f32_one_kernel(const __grid_constant__ GridF32 G, const __grid_constant__ InstF32 P,
                         const InstF32 *inst, int total_tiles, int nsteps, int esc_cache)
@@ -1018,7 +1022,7 @@ __global__ void __launch_bounds__(256, 4)
     const int64_t step0 = *reinterpret_cast<const volatile long long *>(&inst->step0);
     __syncthreads();
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x)
-        run_tile_coll<kExtras, true>(G, P, s_rf, (int64_t)t * blockDim.x, nsteps, s_esc, step0);
+        run_tile_coll<kExtras, true, kW>(G, P, s_rf, (int64_t)t * blockDim.x, nsteps, s_esc, step0);
 }
 
 // Streamed single step over the tiles of one instance (see above). Warp 4
@@ -1236,15 +1240,22 @@ void launch_rf_table(InstF32 *d_insts, int n_inst, int nsteps, cudaStream_t s)
 }
 
 void launch_step_f32_one(const GridF32 &G, const InstF32 &h_inst, const InstF32 *d_inst, int total_tiles,
-                         int threads, int nsteps, int grid, bool extras, bool esc_cache, cudaStream_t s)
+                         int threads, int nsteps, int grid, bool extras, bool esc_cache, int cand_weight,
+                         cudaStream_t s)
 {
     if (total_tiles <= 0) return;
     const size_t smem = step_f32_smem(threads, nsteps, esc_cache);
     const int ec = esc_cache ? 1 : 0;
-    if (extras)
-        step_f32_one_kernel<true><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps, ec);
+    const bool eager = cand_weight == kEagerWeight;
+    if (extras && eager)
+        step_f32_one_kernel<true, kEagerWeight><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps, ec);
+    else if (extras)
+        step_f32_one_kernel<true, 1><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps, ec);
+    else if (eager)
+        step_f32_one_kernel<false, kEagerWeight><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps,
+                                                                           ec);
     else
-        step_f32_one_kernel<false><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps, ec);
+        step_f32_one_kernel<false, 1><<<grid, threads, smem, s>>>(G, h_inst, d_inst, total_tiles, nsteps, ec);
 }
 
 void launch_step_f32_stream(const GridF32 &G, const InstF32 &P, InstF32 *d_insts, int total_tiles, int grid,

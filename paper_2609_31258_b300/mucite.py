@@ -25,9 +25,11 @@ EXPORTS = ["mucite_create", "mucite_destroy", "mucite_last_error", "mucite_load_
            "mucite_step_set", "mucite_autotune",
            "mucite_pic_update", "mucite_tally", "mucite_pic_read", "mucite_set_tuning", "mucite_set_launch_mode",
            "mucite_launch_count", "mucite_sync", "mucite_poisson_solve_noalloc", "mucite_set_dt",
-           "mucite_dt_limits", "mucite_graph_stats", "mucite_set_pic_solver", "mucite_test_hook"]
+           "mucite_dt_limits", "mucite_graph_stats", "mucite_set_pic_solver", "mucite_set_schedule",
+           "mucite_test_hook"]
 HOOK_HOLD_STAGED_COPY = 1
 DST_SIMT, DST_TENSOR_CORES = 0, 1
+SCHEDULE_BALANCED, SCHEDULE_EAGER = 1, 6
 
 
 class MuciteError(RuntimeError):
@@ -75,7 +77,8 @@ class Layout(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("steps_per_launch", C.c_int32), ("threads_per_block", C.c_int32),
-                ("persistent_blocks_per_sm", C.c_int32), ("n_tried", C.c_int32), ("best_ms_per_step", C.c_double)]
+                ("persistent_blocks_per_sm", C.c_int32), ("schedule", C.c_int32), ("n_tried", C.c_int32),
+                ("best_ms_per_step", C.c_double)]
 
 
 _i64p = C.POINTER(C.c_int64)
@@ -126,6 +129,7 @@ def lib():
         L.mucite_sync.argtypes = [vp]
         L.mucite_graph_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.mucite_set_pic_solver.argtypes = [vp, C.c_int]
+        L.mucite_set_schedule.argtypes = [vp, C.c_int]
         L.mucite_test_hook.argtypes = [vp, C.c_int, C.c_int]
         L.mucite_poisson_solve_noalloc.argtypes = [C.c_int, vp, C.POINTER(Grid), vp, vp, vp, vp]
         L.mucite_set_dt.argtypes = [vp, C.c_int, C.c_double]
@@ -316,6 +320,11 @@ class Context:
         """DST_SIMT (default) or DST_TENSOR_CORES for the space-charge solve's
         contractions; after load_fields, before injecting instances."""
         self._check(lib().mucite_set_pic_solver(self._p, int(contraction)))
+
+    def set_schedule(self, schedule):
+        """SCHEDULE_BALANCED (default) or SCHEDULE_EAGER for the collision loop
+        of the per-instance collision launches (results do not depend on it)."""
+        self._check(lib().mucite_set_schedule(self._p, int(schedule)))
 
     def test_hook(self, hook, value):
         """Failure-path test hook (see include/mucite.h); not for production runs."""
