@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
     }
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int st = 8;
+    double wke = 0.0, wte = 0.0, wsy = 0.0; // the pack's weighted KE, T_eff and SY
     if (p < A.n) {
-        const int st = A.status[p];
+        st = A.status[p];
         if (st < 8) {
             int32_t xq, yq, zq;
             double vx, vy, vz, ei, ls;
@@ -90,10 +92,9 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
             const double ke = __dmul_rn(v2, A.c_ke);
             const double te = teff_exact(A.prof, ei);
             const double W = (double)A.weight;
-            atomicAdd(&s_cnt[st], 1ull);
-            atomicAdd(&s_ke[st], W * ke);
-            atomicAdd(&s_te[st], W * te);
-            atomicAdd(&s_sy[st], W * exp(ls));
+            wke = W * ke;
+            wte = W * te;
+            wsy = W * exp(ls);
             const float fx = (float)xq, fy = (float)yq;
             const float rr = __fsqrt_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)));
             const unsigned long long Wu = (unsigned long long)A.weight;
@@ -111,6 +112,31 @@ __global__ void __launch_bounds__(256) tally_kernel(TallyArgs A)
                 atomicAdd(&A.loss_map[bz * A.n_loss_r + br], Wu);
             }
         }
+    }
+    // per status, the warp's packs summed first (lanes of one status at a
+    // time, a butterfly over the warp), then one shared-memory atomic per
+    // status present instead of one per pack
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool valid = st < 8;
+    unsigned todo = __ballot_sync(kAll, valid);
+    while (todo != 0u) {
+        const int src = __ffs(todo) - 1;
+        const int s = __shfl_sync(kAll, st, src);
+        const bool mine = valid && st == s;
+        const unsigned m = __ballot_sync(kAll, mine);
+        double a = mine ? wke : 0.0, b = mine ? wte : 0.0, c = mine ? wsy : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(kAll, a, o);
+            b += __shfl_xor_sync(kAll, b, o);
+            c += __shfl_xor_sync(kAll, c, o);
+        }
+        if ((int)(threadIdx.x & 31u) == src) {
+            atomicAdd(&s_cnt[s], (unsigned long long)__popc(m));
+            atomicAdd(&s_ke[s], a);
+            atomicAdd(&s_te[s], b);
+            atomicAdd(&s_sy[s], c);
+        }
+        todo &= ~m;
     }
     __syncthreads();
     if (threadIdx.x < 8 && s_cnt[threadIdx.x]) {

@@ -337,6 +337,11 @@ class Context:
         return int(r.value), int(c.value)
 
     # -- views of a pack pool -------------------------------------------------
+    def pool(self, instance):
+        """torch uint8 view (no copy) of the instance's whole pool: the buffer
+        whose layout mucite_state_layout gives, for copies of the whole state."""
+        return self.pools[instance][1]
+
     def state(self, instance):
         """torch views (no copy) of the instance's structure-of-arrays pool."""
         torch = self.torch
